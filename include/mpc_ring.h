@@ -1,0 +1,269 @@
+/*
+ * mpc_ring.h - C ABI of the B300 (sm_103a) private ring linear-algebra library.
+ *
+ * The library implements the hot path of CrypTen's secure multi-party
+ * computation (arXiv 2109.00984): additive secret shares over the ring
+ * Z/2^64 with fixed-point encoding (§5.1), Beaver-triple products for
+ * elementwise / matmul / conv (§5.2, App. D.1.1), two-party local truncation
+ * (App. D.1.1), and the comparison behind private ReLU: A2B with a
+ * carry-lookahead adder, the sign bit, single-bit B2A (Alg. 2) and a Beaver
+ * product with the mask (§5.2 "Comparators", App. D.1.2-D.1.4).
+ * All parties are simulated on one GPU; "opening" a masked value is a
+ * device-local reduction over the party axis, fused into the consuming kernel.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: MPC_OK (0) or a negative mpc_status.  The message of the
+ *    last failure on the calling thread is returned by mpc_last_error().
+ *  - Validation happens on the host before anything is launched; a call that
+ *    returns an error has launched nothing (except MPC_ECUDA, reported when a
+ *    launch itself failed).
+ *  - Ownership: the caller owns every buffer, including workspaces sized by
+ *    the mpc_*_workspace_size() functions.  Unless an entry point says
+ *    otherwise, the library never allocates or frees memory.
+ *  - Pointers marked "device" must point to memory of the current CUDA
+ *    device.  Nothing synchronises: every call is asynchronous on `stream`
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream), except
+ *    mpc_sync_status().
+ *  - Shares are uint64 words, party-major and C-contiguous: a tensor of
+ *    shape S held by P parties is laid out as [P][S].  Public ring tensors
+ *    are [S].  Ring arithmetic wraps modulo 2^64; s(.) is the two's-complement
+ *    signed view.
+ *  - Randomness is explicit.  Every random word is word j of a Philox4x64-10
+ *    stream (Salmon et al., SC'11) with key (seed, 0) and counter
+ *    (j / 4, op_id, (role << 32) | (sub << 8) | party, 0), output word j % 4.
+ *    The roles are the MPC_ROLE_* values below.  Equal (seed, op_id) give
+ *    bit-identical results; callers must not reuse an op_id for two pieces
+ *    of material.
+ *  - Errors found on the device (an out-of-range real in mpc_ring_share, a
+ *    bounded wait that gave up) are recorded in a per-device status word and
+ *    returned by the next mpc_sync_status().
+ *  - Parties: 1 <= P <= MPC_MAX_PARTIES.  The binary-share calls (mpc_a2b,
+ *    mpc_private_relu) support P = 2 only (one carry-lookahead adder).
+ */
+#ifndef MPC_RING_H
+#define MPC_RING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPC_MAX_PARTIES 8
+#define MPC_KS_GATES 12 /* secret ANDs in one 64-bit Kogge-Stone adder */
+
+typedef enum {
+  MPC_OK = 0,
+  MPC_EINVAL = -1,      /* bad argument: null pointer, size, party count ... */
+  MPC_ERANGE = -2,      /* a real value does not fit the fixed-point range   */
+  MPC_ENOMEM = -3,      /* caller-provided workspace too small               */
+  MPC_ECUDA = -4,       /* a CUDA runtime call or kernel launch failed       */
+  MPC_ETIMEOUT = -5,    /* a bounded device-side wait gave up                */
+  MPC_EUNSUPPORTED = -6 /* valid request this build does not implement       */
+} mpc_status;
+
+/* Ring GEMM engines for matmul / conv. */
+typedef enum {
+  MPC_ALGO_PLAIN = 0, /* CUDA-core 64-bit multiply-add emulated on 32-bit IMAD */
+  MPC_ALGO_LIMB = 1,  /* 8-bit limb split on tcgen05 tensor cores              */
+  MPC_ALGO_AUTO = 2   /* library picks (LIMB where the shape allows)           */
+} mpc_algo;
+
+/* PRG stream roles (third counter word bits 32..63). */
+enum {
+  MPC_ROLE_ZERO_ARITH = 0, /* arithmetic zero-share                         */
+  MPC_ROLE_ZERO_BIN = 1,   /* binary zero-share in A2B, sub = owner q       */
+  MPC_ROLE_TRIPLE_A = 2,
+  MPC_ROLE_TRIPLE_B = 3,
+  MPC_ROLE_TRIPLE_C = 4,
+  MPC_ROLE_AND_A = 5, /* sub = gate index */
+  MPC_ROLE_AND_B = 6,
+  MPC_ROLE_AND_C = 7,
+  MPC_ROLE_B2A_R = 8, /* party = MPC_TTP_PARTY: the dealer's secret bit */
+  MPC_ROLE_B2A_BIN = 9,
+  MPC_ROLE_B2A_ARITH = 10
+};
+#define MPC_TTP_PARTY 255
+
+/* Convolution geometry (NCHW data, OIHW weights, cross-correlation, zero
+ * padding, groups = 1, dilation = 1).  A 1-D convolution is H = 1, kh = 1,
+ * pad_h = 0. */
+typedef struct {
+  int64_t batch, c_in, h, w;  /* data  [batch][c_in][h][w]     */
+  int64_t c_out, kh, kw;      /* weight [c_out][c_in][kh][kw]  */
+  int64_t stride_h, stride_w; /* >= 1                          */
+  int64_t pad_h, pad_w;       /* >= 0                          */
+} mpc_conv_desc;
+
+/* Counters of the protocol's communication, accumulated per process.
+ * Rounds follow Table 3 of the paper: multiplication 1, AND 1, two-party
+ * truncation 0, A2B 7 (one generate round + log2(64) prefix rounds), B2A 1. */
+typedef struct {
+  uint64_t calls;
+  uint64_t rounds;              /* sequential opening rounds                */
+  uint64_t bytes_opened;        /* bytes each party broadcasts               */
+  uint64_t and_gates;           /* secret 64-bit AND word-gates evaluated    */
+  uint64_t triple_words;        /* dealer words consumed by online calls     */
+  uint64_t ring_macs;           /* multiply-adds in ring GEMMs (all parties) */
+  uint64_t launches;            /* kernels launched by the library           */
+} mpc_stats_t;
+
+/* ---- status / diagnostics ------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mpc_last_error(void);
+
+/* Synchronises `stream`, then returns and clears the current device's
+ * device-side status word (MPC_OK, MPC_ERANGE or MPC_ETIMEOUT), or MPC_ECUDA
+ * if the stream reports an error. */
+int mpc_sync_status(void* stream);
+
+/* Copies the accumulated counters; mpc_reset_stats() zeroes them. */
+int mpc_get_stats(mpc_stats_t* out);
+int mpc_reset_stats(void);
+
+/* Per-kernel timing.  While enabled, each launch of a timed kernel is
+ * bracketed by two CUDA events on its stream (no synchronisation).
+ * mpc_profile_read() waits for those events and returns, for the kernel
+ * `kernel` ("gemm_plain", "gemm_limb", "limb_planes", "private_relu",
+ * "beaver_mul", "a2b"), the number of launches and their summed device time
+ * since the last mpc_profile_reset().  Not for use inside stream capture. */
+int mpc_profile_enable(int on);
+int mpc_profile_reset(void);
+int mpc_profile_read(const char* kernel, uint64_t* launches, double* total_ms);
+
+/* ---- sharing / reveal (§5.1, App. D.1.1) --------------------------------- */
+
+/* Encode and share reals.  x: device double[n].  shares: device u64 [P][n].
+ * x_enc = rint(x * 2^frac_bits) (ties to even); R_p = stream(ZERO_ARITH,
+ * party p); shares[p] = R_p - R_{(p-1) mod P} + (p == src ? x_enc : 0).
+ * |x * 2^frac_bits| >= 2^63 or a non-finite x stores 0 for that element and
+ * records MPC_ERANGE for mpc_sync_status().  0 <= frac_bits <= 62. */
+int mpc_ring_share(const double* x, int64_t n, int P, int src, int frac_bits, uint64_t seed,
+                   uint64_t op_id, uint64_t* shares, void* stream);
+
+/* Share ring elements that are already encoded: as mpc_ring_share without
+ * the encoding step.  x_ring: device u64[n]. */
+int mpc_ring_share_encoded(const uint64_t* x_ring, int64_t n, int P, int src, uint64_t seed,
+                           uint64_t op_id, uint64_t* shares, void* stream);
+
+/* Open shares: ring_out[i] = sum_p shares[p][i] (mod 2^64) and/or
+ * real_out[i] = (double)s(ring value) / 2^frac_bits.  Either output may be
+ * NULL, not both.  All pointers device. */
+int mpc_reveal(const uint64_t* shares, int P, int64_t n, int frac_bits, uint64_t* ring_out,
+               double* real_out, void* stream);
+
+/* ---- dealer / trusted third party (§4, App. D.1.1-D.1.3) ----------------- */
+
+/* Elementwise Beaver triple: A, B, C device u64 [P][n]; A[p] = stream(TRIPLE_A,
+ * p), B[p] = stream(TRIPLE_B, p), c = (sum A)(sum B), C[p] = stream(TRIPLE_C, p)
+ * for p < P-1 and C[P-1] = c - sum_{p<P-1} C[p]. */
+int mpc_ttp_mul_triple(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* A,
+                       uint64_t* B, uint64_t* C, void* stream);
+
+/* Matmul triple: A [P][M][K], B [P][K][N], C [P][M][N] (device), c = a b, the
+ * streams and the correction as for mpc_ttp_mul_triple (word index = flat
+ * element index).  ws: device workspace of mpc_matmul_triple_workspace_size()
+ * bytes.  algo selects the ring GEMM engine for c. */
+size_t mpc_matmul_triple_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo);
+int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed,
+                          uint64_t op_id, uint64_t* A, uint64_t* B, uint64_t* C, int algo,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Convolution triple: A data-shaped [P][batch][c_in][h][w], B weight-shaped
+ * [P][c_out][c_in][kh][kw], C output-shaped [P][batch][c_out][ho][wo], with
+ * c = conv2d(a, b) over the ring. */
+size_t mpc_conv2d_triple_workspace_size(int P, const mpc_conv_desc* d, int algo);
+int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t op_id,
+                          uint64_t* A, uint64_t* B, uint64_t* C, int algo, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/* Binary AND triples for `gates` gates over n words: T device u64
+ * [gates][3][P][n] holding (a, b, c) per gate, a and b from the AND_A/AND_B
+ * streams (sub = gate), c = (xor_p a_p) & (xor_p b_p) shared with AND_C
+ * words for p < P-1 and the XOR correction on party P-1. */
+int mpc_ttp_and_triples(int P, int64_t n, int gates, uint64_t seed, uint64_t op_id,
+                        uint64_t* T, void* stream);
+
+/* Random-bit pairs for B2A (App. D.1.3, Alg. 2): r = bit 0 of
+ * stream(B2A_R, party MPC_TTP_PARTY); r_arith device u64 [P][n] with
+ * r_arith[p] = stream(B2A_ARITH, p) for p < P-1 and r - sum on P-1;
+ * r_bin device u64 [P][(n + 63) / 64], bit (i % 64) of word i / 64 of party
+ * p = bit 0 of stream(B2A_BIN, p) word i for p < P-1, XOR-corrected on P-1.
+ * Unused tail bits of r_bin are 0. */
+int mpc_ttp_b2a_bits(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* r_arith,
+                     uint64_t* r_bin, void* stream);
+
+/* ---- online arithmetic (§5.2, App. D.1.1) -------------------------------- */
+
+/* Fused elementwise Beaver product: one pass reads X, Y, A, B, C (device u64
+ * [P][n]), opens E = sum_p (X_p - A_p) and F = sum_p (Y_p - B_p) in
+ * registers, and writes Z_p = C_p + E B_p + A_p F (+ E F on party 0), then,
+ * if trunc_bits > 0, Z_p = s(Z_p) >> trunc_bits (two-party local
+ * truncation).  E_out / F_out (device u64[n]) receive the opened values when
+ * not NULL.  Z may alias X or Y. */
+int mpc_beaver_mul(int P, int64_t n, const uint64_t* X, const uint64_t* Y, const uint64_t* A,
+                   const uint64_t* B, const uint64_t* C, uint64_t* Z, uint64_t* E_out,
+                   uint64_t* F_out, int trunc_bits, void* stream);
+
+/* Beaver matmul: X [P][M][K], Y [P][K][N], triple A [P][M][K], B [P][K][N],
+ * C [P][M][N], Z [P][M][N] (device).  Z_p = C_p + E B_p + A_p F (+ E F on
+ * party 0) with E = sum(X - A), F = sum(Y - B), optionally truncated by
+ * trunc_bits.  ws: device workspace of mpc_matmul_workspace_size() bytes. */
+size_t mpc_matmul_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo);
+int mpc_beaver_matmul(int P, int64_t M, int64_t N, int64_t K, const uint64_t* X,
+                      const uint64_t* Y, const uint64_t* A, const uint64_t* B,
+                      const uint64_t* C, uint64_t* Z, int algo, int trunc_bits, void* ws,
+                      size_t ws_bytes, void* stream);
+
+/* Beaver convolution (App. D.1.1: the identity holds for any bilinear f):
+ * X data [P][batch][c_in][h][w], W weights [P][c_out][c_in][kh][kw], triple
+ * A (data-shaped), B (weight-shaped), C (output-shaped), Z output
+ * [P][batch][c_out][ho][wo]; all device. */
+size_t mpc_conv2d_workspace_size(int P, const mpc_conv_desc* d, int algo);
+int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                      const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
+                      int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream);
+
+/* Plain ring GEMM Z = C + A B over Z/2^64: A [M][K], B [K][N], C [M][N] or
+ * NULL, Z [M][N] (device, row-major).  ws as mpc_ring_gemm_workspace_size(). */
+size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo);
+int mpc_ring_gemm(int64_t M, int64_t N, int64_t K, const uint64_t* A, const uint64_t* B,
+                  const uint64_t* C, uint64_t* Z, int algo, void* ws, size_t ws_bytes,
+                  void* stream);
+
+/* Two-party local truncation (App. D.1.1), in place on device u64 [P][n]:
+ * share = floor(s(share) / l) with l = divisor if divisor > 0, else
+ * 2^frac_bits (an arithmetic shift).  0 <= frac_bits <= 63. */
+int mpc_truncate(int P, int64_t n, uint64_t* shares, int frac_bits, int64_t divisor,
+                 void* stream);
+
+/* ---- binary shares and comparison (§5.1-5.2, App. D.1.2-D.1.4) ---------- */
+
+/* A2B for P = 2: arith [2][n] -> binary [2][n] (device).  Each party's share
+ * y_q is binary-shared with the ZERO_BIN stream (sub = q): party p holds
+ * M_{q,p} ^ M_{q,(p-1) mod 2} ^ (p == q ? y_q : 0); the two binary-shared
+ * words are added by a 64-bit Kogge-Stone adder whose 12 secret ANDs use
+ * and_triples [12][3][2][n] (mpc_ttp_and_triples) in the order: generate,
+ * then for d = 1, 2, 4, 8, 16, 32 the G-update and (d < 32) the P-update. */
+int mpc_a2b(int P, int64_t n, const uint64_t* arith, uint64_t* binary,
+            const uint64_t* and_triples, uint64_t seed, uint64_t op_id, void* stream);
+
+/* Private ReLU for P = 2, fused in one kernel: [x > 0] = B2A(MSB(A2B(-x)))
+ * (comparator of §5.2, Alg. 2), then Y = Beaver product of X with the 0/1
+ * mask (not truncated).  X, Y device u64 [2][n] (may alias); and_triples
+ * [12][3][2][n]; r_arith [2][n] and r_bin [2][(n+63)/64] from
+ * mpc_ttp_b2a_bits; mul_triple [3][2][n] = (A, B, C) from mpc_ttp_mul_triple
+ * laid out consecutively.  (seed, op_id) drive the A2B binary zero-shares. */
+int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
+                     const uint64_t* and_triples, const uint64_t* r_arith,
+                     const uint64_t* r_bin, const uint64_t* mul_triple, uint64_t seed,
+                     uint64_t op_id, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPC_RING_H */

@@ -1,0 +1,275 @@
+"""Python binding: argument marshalling from torch CUDA tensors to the C ABI.
+
+Every function here only checks tensors, allocates outputs/workspaces with
+torch (the caller's memory), and calls the entry point of the same name in
+libmpcring.so on torch's current CUDA stream.  Ring words are carried in
+torch.int64 (or torch.uint64) tensors: the bit pattern is the uint64 value.
+No arithmetic of the protocol happens in Python.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+PLAIN, LIMB, AUTO = 0, 1, 2
+KS_GATES = 12
+MAX_PARTIES = 8
+
+MPC_OK = 0
+STATUS_NAMES = {0: "MPC_OK", -1: "MPC_EINVAL", -2: "MPC_ERANGE", -3: "MPC_ENOMEM", -4: "MPC_ECUDA",
+                -5: "MPC_ETIMEOUT", -6: "MPC_EUNSUPPORTED"}
+
+
+class MPCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _L():
+    return _lib.load()
+
+
+def _check(rc):
+    if rc != MPC_OK:
+        raise MPCError(rc, _L().mpc_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+_WORD_DTYPES = (torch.int64, torch.uint64)
+
+
+def _ptr(t, name="tensor", dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is None and t.dtype not in _WORD_DTYPES:
+        raise ValueError(f"{name} must hold 64-bit ring words (int64/uint64), got {t.dtype}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _words(shape, device):
+    return torch.empty(shape, dtype=torch.int64, device=device)
+
+
+def _ws(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def conv_desc(batch, c_in, h, w, c_out, kh, kw, stride_h=1, stride_w=1, pad_h=0, pad_w=0):
+    return _lib.ConvDesc(batch, c_in, h, w, c_out, kh, kw, stride_h, stride_w, pad_h, pad_w)
+
+
+def conv_out_hw(d):
+    return ((d.h + 2 * d.pad_h - d.kh) // d.stride_h + 1,
+            (d.w + 2 * d.pad_w - d.kw) // d.stride_w + 1)
+
+
+# ---- status / counters ------------------------------------------------------------
+def sync_status():
+    """Synchronise the current stream and raise on a device-side error."""
+    _check(_L().mpc_sync_status(_stream()))
+
+
+def get_stats():
+    s = _lib.Stats()
+    _check(_L().mpc_get_stats(ctypes.byref(s)))
+    return {f: int(getattr(s, f)) for f, _ in _lib.Stats._fields_}
+
+
+def reset_stats():
+    _check(_L().mpc_reset_stats())
+
+
+def profile_enable(on=True):
+    _check(_L().mpc_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(_L().mpc_profile_reset())
+
+
+def profile_read(kernel):
+    """(launches, total_ms) of a timed kernel since the last profile_reset()."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(_L().mpc_profile_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+# ---- sharing / reveal ---------------------------------------------------------------
+def ring_share(x, P, src, seed, op_id, frac_bits=16, out=None):
+    """Encode float64 reals x (CUDA) and share among P parties -> [P, *x.shape]."""
+    n = x.numel()
+    out = _words((P,) + tuple(x.shape), x.device) if out is None else out
+    _check(_L().mpc_ring_share(_ptr(x, "x", torch.float64), n, P, src, frac_bits, seed, op_id,
+                               _ptr(out, "out"), _stream()))
+    return out
+
+
+def ring_share_encoded(x_ring, P, src, seed, op_id, out=None):
+    n = x_ring.numel()
+    out = _words((P,) + tuple(x_ring.shape), x_ring.device) if out is None else out
+    _check(_L().mpc_ring_share_encoded(_ptr(x_ring, "x_ring"), n, P, src, seed, op_id,
+                                       _ptr(out, "out"), _stream()))
+    return out
+
+
+def reveal(shares, frac_bits=16, ring=False, real=True):
+    """Open [P, ...] shares; returns (ring or None, real or None)."""
+    P = shares.shape[0]
+    shape = tuple(shares.shape[1:])
+    n = shares.numel() // P
+    r = _words(shape, shares.device) if ring else None
+    f = torch.empty(shape, dtype=torch.float64, device=shares.device) if real else None
+    _check(_L().mpc_reveal(_ptr(shares, "shares"), P, n, frac_bits, _ptr(r),
+                           _ptr(f, "real", torch.float64) if f is not None else None, _stream()))
+    return r, f
+
+
+# ---- dealer ---------------------------------------------------------------------------
+def ttp_mul_triple(P, n, seed, op_id, device="cuda", out=None):
+    A, B, C = out if out is not None else (_words((P, n), device) for _ in range(3))
+    _check(_L().mpc_ttp_mul_triple(P, n, seed, op_id, _ptr(A), _ptr(B), _ptr(C), _stream()))
+    return A, B, C
+
+
+def ttp_matmul_triple(P, M, N, K, seed, op_id, algo=PLAIN, device="cuda", out=None, ws=None):
+    A, B, C = out if out is not None else (_words((P, M, K), device), _words((P, K, N), device),
+                                           _words((P, M, N), device))
+    need = _L().mpc_matmul_triple_workspace_size(P, M, N, K, algo)
+    ws = _ws(need, device) if ws is None else ws
+    _check(_L().mpc_ttp_matmul_triple(P, M, N, K, seed, op_id, _ptr(A), _ptr(B), _ptr(C), algo,
+                                      _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return A, B, C
+
+
+def ttp_conv2d_triple(P, d, seed, op_id, algo=PLAIN, device="cuda", out=None, ws=None):
+    ho, wo = conv_out_hw(d)
+    if out is None:
+        A = _words((P, d.batch, d.c_in, d.h, d.w), device)
+        B = _words((P, d.c_out, d.c_in, d.kh, d.kw), device)
+        C = _words((P, d.batch, d.c_out, ho, wo), device)
+    else:
+        A, B, C = out
+    need = _L().mpc_conv2d_triple_workspace_size(P, ctypes.byref(d), algo)
+    ws = _ws(need, device) if ws is None else ws
+    _check(_L().mpc_ttp_conv2d_triple(P, ctypes.byref(d), seed, op_id, _ptr(A), _ptr(B), _ptr(C),
+                                      algo, _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return A, B, C
+
+
+def ttp_and_triples(P, n, seed, op_id, gates=KS_GATES, device="cuda", out=None):
+    T = _words((gates, 3, P, n), device) if out is None else out
+    _check(_L().mpc_ttp_and_triples(P, n, gates, seed, op_id, _ptr(T), _stream()))
+    return T
+
+
+def ttp_b2a_bits(P, n, seed, op_id, device="cuda", out=None):
+    if out is None:
+        ra, rb = _words((P, n), device), _words((P, (n + 63) // 64), device)
+    else:
+        ra, rb = out
+    _check(_L().mpc_ttp_b2a_bits(P, n, seed, op_id, _ptr(ra), _ptr(rb), _stream()))
+    return ra, rb
+
+
+# ---- online arithmetic -------------------------------------------------------------------
+def beaver_mul(X, Y, A, B, C, trunc_bits=0, out=None, E_out=None, F_out=None):
+    P = X.shape[0]
+    n = X.numel() // P
+    Z = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_beaver_mul(P, n, _ptr(X), _ptr(Y), _ptr(A), _ptr(B), _ptr(C), _ptr(Z),
+                               _ptr(E_out), _ptr(F_out), trunc_bits, _stream()))
+    return Z
+
+
+def beaver_matmul(X, Y, A, B, C, algo=PLAIN, trunc_bits=0, out=None, ws=None):
+    P, M, K = X.shape
+    N = Y.shape[2]
+    Z = _words((P, M, N), X.device) if out is None else out
+    need = _L().mpc_matmul_workspace_size(P, M, N, K, algo)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_matmul(P, M, N, K, _ptr(X), _ptr(Y), _ptr(A), _ptr(B), _ptr(C),
+                                  _ptr(Z), algo, trunc_bits, _ptr(ws, "ws", torch.uint8),
+                                  ws.numel(), _stream()))
+    return Z
+
+
+def beaver_conv2d(X, W, A, B, C, d, algo=PLAIN, trunc_bits=0, out=None, ws=None):
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Z = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), algo)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d(P, ctypes.byref(d), _ptr(X), _ptr(W), _ptr(A), _ptr(B), _ptr(C),
+                                  _ptr(Z), algo, trunc_bits, _ptr(ws, "ws", torch.uint8),
+                                  ws.numel(), _stream()))
+    return Z
+
+
+def conv2d_workspace_size(P, d, algo=PLAIN):
+    return int(_L().mpc_conv2d_workspace_size(P, ctypes.byref(d), algo))
+
+
+def conv2d_triple_workspace_size(P, d, algo=PLAIN):
+    return int(_L().mpc_conv2d_triple_workspace_size(P, ctypes.byref(d), algo))
+
+
+def matmul_workspace_size(P, M, N, K, algo=PLAIN):
+    return int(_L().mpc_matmul_workspace_size(P, M, N, K, algo))
+
+
+def ring_gemm(A, B, C=None, algo=PLAIN, out=None, ws=None):
+    M, K = A.shape
+    N = B.shape[1]
+    Z = _words((M, N), A.device) if out is None else out
+    need = _L().mpc_ring_gemm_workspace_size(M, N, K, algo)
+    ws = _ws(need, A.device) if ws is None else ws
+    _check(_L().mpc_ring_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(C), _ptr(Z), algo,
+                              _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return Z
+
+
+def ring_gemm_workspace_size(M, N, K, algo=PLAIN):
+    return int(_L().mpc_ring_gemm_workspace_size(M, N, K, algo))
+
+
+def truncate(shares, frac_bits=16, divisor=0):
+    """In place on [P, ...] shares; returns shares."""
+    P = shares.shape[0]
+    _check(_L().mpc_truncate(P, shares.numel() // P, _ptr(shares), frac_bits, divisor, _stream()))
+    return shares
+
+
+# ---- binary / comparison -----------------------------------------------------------------
+def a2b(X, and_triples, seed, op_id, out=None):
+    P = X.shape[0]
+    n = X.numel() // P
+    out = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_a2b(P, n, _ptr(X), _ptr(out), _ptr(and_triples), seed, op_id, _stream()))
+    return out
+
+
+def private_relu(X, and_triples, r_arith, r_bin, mul_triple, seed, op_id, out=None):
+    """mul_triple: a [3, P, n] tensor (A, B, C stacked) or a tuple of three [P, n]."""
+    P = X.shape[0]
+    n = X.numel() // P
+    if isinstance(mul_triple, (tuple, list)):
+        mt = torch.stack([t.reshape(P, n) for t in mul_triple])
+    else:
+        mt = mul_triple
+    out = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_private_relu(P, n, _ptr(X), _ptr(out), _ptr(and_triples), _ptr(r_arith),
+                                 _ptr(r_bin), _ptr(mt), seed, op_id, _stream()))
+    return out

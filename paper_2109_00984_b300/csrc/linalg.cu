@@ -1,0 +1,453 @@
+// Beaver matmul / conv and their dealer triples (App. D.1.1: the Beaver
+// identity holds for any bilinear f).  Opening pre-passes, im2col and dealer
+// fills live here; the ring GEMM itself is one of the two engines.
+//
+// Regrouping used for every party p (bit-identical mod 2^64):
+//   Z_p = C_p + E B_p + A_p F + [p = 0] E F = C_p + E (B_p + [p = 0] F) + A_p F
+// so each party runs one two-pair ring GEMM.  For conv, f(x, w) = W_mat *
+// im2col(x), which gives Z_p = C_p + (B_p + [p=0] F)_mat im2col(E) + F_mat im2col(A_p).
+#include "gemm.hpp"
+#include "host.hpp"
+
+namespace mpc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// out[i] = sum_p (X_p[i] - A_p[i]) (opening); if G: G[i] = B0[i] + out[i].
+template <int P>
+__global__ void __launch_bounds__(kThreads) open_kernel(i64 n, const u64* __restrict__ X,
+                                                        const u64* __restrict__ A,
+                                                        u64* __restrict__ out,
+                                                        const u64* __restrict__ B0,
+                                                        u64* __restrict__ G) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    u64 e = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) e += X[(i64)p * n + i] - A[(i64)p * n + i];
+    out[i] = e;
+    if (G) G[i] = B0[i] + e;
+  }
+}
+
+template <int P>
+void launch_open(i64 n, const u64* X, const u64* A, u64* out, const u64* B0, u64* G,
+                 cudaStream_t s) {
+  open_kernel<P><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, X, A, out, B0, G);
+}
+
+// Dealer fill: Out[p] = stream(role, p) for all p and, if sum != null,
+// sum = sum_p Out[p].  One thread per Philox block.
+__global__ void __launch_bounds__(kThreads) fill_sum_kernel(int P, i64 n, u64 seed, u64 op_id,
+                                                            unsigned role, u64* __restrict__ Out,
+                                                            u64* __restrict__ sum) {
+  const i64 nblk = ceil_div(n, 4);
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
+       t += (i64)gridDim.x * blockDim.x) {
+    const i64 i0 = 4 * t;
+    u64 acc[4] = {0, 0, 0, 0};
+    for (int p = 0; p < P; ++p) {
+      const u64x4 r = prg_block(seed, op_id, stream_word2(role, 0, p), t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (i0 + j < n) Out[(i64)p * n + i0 + j] = r.v[j];
+        acc[j] += r.v[j];
+      }
+    }
+    if (sum) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < n) sum[i0 + j] = acc[j];
+    }
+  }
+}
+
+// Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1; C[P-1] holds c on
+// entry and becomes c - sum_{p<P-1} C[p].
+__global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u64 seed,
+                                                                 u64 op_id, u64* __restrict__ C) {
+  const i64 nblk = ceil_div(n, 4);
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
+       t += (i64)gridDim.x * blockDim.x) {
+    const i64 i0 = 4 * t;
+    u64 acc[4] = {0, 0, 0, 0};
+    for (int p = 0; p < P - 1; ++p) {
+      const u64x4 r = prg_block(seed, op_id, stream_word2(MPC_ROLE_TRIPLE_C, 0, p), t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (i0 + j < n) C[(i64)p * n + i0 + j] = r.v[j];
+        acc[j] += r.v[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i0 + j < n) C[(i64)(P - 1) * n + i0 + j] -= acc[j];
+  }
+}
+
+// im2col over the ring: col[k][c] with k = (ci * kh + r) * kw + s and
+// c = (b * ho + oh) * wo + ow, value = sum_{q < nsrc} (src_q - sub_q) at data
+// position (b, ci, oh * sh + r - ph, ow * sw + s - pw), 0 in the padding.
+// sub may be null (no subtraction).  src_q = src + q * src_stride.
+struct Im2colSrc {
+  const u64* src;
+  const u64* sub;
+  i64 stride;  // elements between consecutive parties
+  int nsrc;
+};
+
+__global__ void __launch_bounds__(kThreads) im2col_kernel(mpc_conv_desc d, i64 ho, i64 wo,
+                                                          Im2colSrc in, u64* __restrict__ col) {
+  const i64 ncol = d.batch * ho * wo;
+  const i64 K = d.c_in * d.kh * d.kw;
+  const i64 total = K * ncol;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
+       i += (i64)gridDim.x * blockDim.x) {
+    const i64 k = i / ncol, c = i % ncol;
+    const i64 s = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
+    const i64 ow = c % wo, oh = (c / wo) % ho, b = c / (wo * ho);
+    const i64 y = oh * d.stride_h + r - d.pad_h, x = ow * d.stride_w + s - d.pad_w;
+    u64 v = 0;
+    if (y >= 0 && y < d.h && x >= 0 && x < d.w) {
+      const i64 off = ((b * d.c_in + ci) * d.h + y) * d.w + x;
+      for (int q = 0; q < in.nsrc; ++q) {
+        v += in.src[q * in.stride + off];
+        if (in.sub) v -= in.sub[q * in.stride + off];
+      }
+    }
+    col[i] = v;
+  }
+}
+
+int launch_im2col(const mpc_conv_desc& d, i64 ho, i64 wo, const Im2colSrc& in, u64* col,
+                  cudaStream_t s) {
+  const i64 total = d.c_in * d.kh * d.kw * d.batch * ho * wo;
+  if (total == 0) return MPC_OK;
+  im2col_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(d, ho, wo, in, col);
+  return check_launch("im2col");
+}
+
+int validate_conv(const mpc_conv_desc* d, i64* ho, i64* wo) {
+  MPC_REQUIRE(d != nullptr, "null conv descriptor");
+  MPC_REQUIRE(d->batch >= 1 && d->c_in >= 1 && d->h >= 1 && d->w >= 1 && d->c_out >= 1 &&
+                  d->kh >= 1 && d->kw >= 1,
+              "conv sizes must be positive");
+  MPC_REQUIRE(d->stride_h >= 1 && d->stride_w >= 1, "conv strides must be >= 1");
+  MPC_REQUIRE(d->pad_h >= 0 && d->pad_w >= 0, "conv padding must be >= 0");
+  MPC_REQUIRE(d->h + 2 * d->pad_h >= d->kh && d->w + 2 * d->pad_w >= d->kw,
+              "kernel larger than the padded input");
+  *ho = (d->h + 2 * d->pad_h - d->kh) / d->stride_h + 1;
+  *wo = (d->w + 2 * d->pad_w - d->kw) / d->stride_w + 1;
+  return MPC_OK;
+}
+
+int resolve_algo(int algo, i64 M, i64 N, i64 K) {
+  if (algo == MPC_ALGO_AUTO) return limb_supported(M, N, K) ? MPC_ALGO_LIMB : MPC_ALGO_PLAIN;
+  return algo;
+}
+
+int run_gemm(const GemmArgs& g, int algo, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (algo == MPC_ALGO_LIMB) return launch_gemm_limb(g, ws, ws_bytes, s);
+  return launch_gemm_plain(g, s);
+}
+
+size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
+  return algo == MPC_ALGO_LIMB ? limb_workspace_bytes(M, N, K, npairs, njobs) : 0;
+}
+
+inline size_t words(i64 n) { return (size_t)n * sizeof(u64); }
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Workspace carving (each region 256-byte aligned).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* p) : base(static_cast<char*>(p)) {}
+  u64* take(i64 nwords) {
+    u64* p = reinterpret_cast<u64*>(base + off);
+    off += align256(words(nwords));
+    return p;
+  }
+  void* rest() { return base + off; }
+};
+
+size_t matmul_ws(int P, i64 M, i64 N, i64 K, int algo) {
+  (void)P;
+  return align256(words(M * K)) + 2 * align256(words(K * N)) + engine_ws(algo, M, N, K, 2, P);
+}
+
+size_t conv_ws(int P, const mpc_conv_desc& d, i64 ho, i64 wo, int algo) {
+  const i64 M = d.c_out, K = d.c_in * d.kh * d.kw, N = d.batch * ho * wo;
+  return (size_t)(P + 1) * align256(words(K * N)) + 2 * align256(words(M * K)) +
+         engine_ws(algo, M, N, K, 2, P);
+}
+
+size_t matmul_triple_ws(i64 M, i64 N, i64 K, int algo) {
+  return align256(words(M * K)) + align256(words(K * N)) + engine_ws(algo, M, N, K, 1, 1);
+}
+
+size_t conv_triple_ws(const mpc_conv_desc& d, i64 ho, i64 wo, int algo) {
+  const i64 M = d.c_out, K = d.c_in * d.kh * d.kw, N = d.batch * ho * wo;
+  const i64 nx = d.batch * d.c_in * d.h * d.w;
+  return align256(words(nx)) + align256(words(K * N)) + align256(words(M * K)) +
+         engine_ws(algo, M, N, K, 1, 1);
+}
+
+int check_algo(int algo) {
+  MPC_REQUIRE(algo == MPC_ALGO_PLAIN || algo == MPC_ALGO_LIMB || algo == MPC_ALGO_AUTO,
+              "unknown algo %d", algo);
+  return MPC_OK;
+}
+
+}  // namespace
+
+}  // namespace mpc
+
+using namespace mpc;
+
+extern "C" {
+
+size_t mpc_matmul_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo) {
+  if (P < 1 || P > MPC_MAX_PARTIES || M < 0 || N < 0 || K < 0) return 0;
+  return matmul_ws(P, M, N, K, resolve_algo(algo, M, N, K));
+}
+
+int mpc_beaver_matmul(int P, int64_t M, int64_t N, int64_t K, const uint64_t* X,
+                      const uint64_t* Y, const uint64_t* A, const uint64_t* B, const uint64_t* C,
+                      uint64_t* Z, int algo, int trunc_bits, void* ws, size_t ws_bytes,
+                      void* stream) {
+  MPC_CHECK_PARTIES(P);
+  if (int rc = check_algo(algo)) return rc;
+  MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  if (M == 0 || N == 0) return MPC_OK;
+  MPC_REQUIRE(X && Y && A && B && C && Z, "null pointer");
+  algo = resolve_algo(algo, M, N, K);
+  if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support M=%lld N=%lld K=%lld",
+                (long long)M, (long long)N, (long long)K);
+  const size_t need = matmul_ws(P, M, N, K, algo);
+  MPC_REQUIRE(ws != nullptr || need == 0, "null workspace");
+  if (ws_bytes < need)
+    return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  u64* E = cv.take(M * K);
+  u64* F = cv.take(K * N);
+  u64* G = cv.take(K * N);
+  if (K > 0) {
+    MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)X, (const u64*)A, E, nullptr, nullptr, s);
+    if (int rc = check_launch("open E")) return rc;
+    MPC_DISPATCH_P(P, launch_open, K * N, (const u64*)Y, (const u64*)B, F, (const u64*)B, G, s);
+    if (int rc = check_launch("open F")) return rc;
+  }
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.hw_out = 0;
+  g.trunc_bits = trunc_bits;
+  g.njobs = P;
+  for (int p = 0; p < P; ++p) {
+    g.jobs[p].A1 = E;
+    g.jobs[p].B1 = p == 0 ? G : (const u64*)B + (i64)p * K * N;
+    g.jobs[p].A2 = (const u64*)A + (i64)p * M * K;
+    g.jobs[p].B2 = F;
+    g.jobs[p].C = (const u64*)C + (i64)p * M * N;
+    g.jobs[p].Z = (u64*)Z + (i64)p * M * N;
+  }
+  int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s);
+  if (rc == MPC_OK)
+    stats_add(1, 8ull * (uint64_t)(M * K + K * N), 0, (uint64_t)P * (M * K + K * N + M * N),
+              (uint64_t)P * 2ull * M * N * K);
+  return rc;
+}
+
+size_t mpc_conv2d_workspace_size(int P, const mpc_conv_desc* d, int algo) {
+  i64 ho, wo;
+  if (P < 1 || P > MPC_MAX_PARTIES || validate_conv(d, &ho, &wo) != MPC_OK) return 0;
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  return conv_ws(P, *d, ho, wo, resolve_algo(algo, M, N, K));
+}
+
+int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                      const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
+                      int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  if (int rc = check_algo(algo)) return rc;
+  i64 ho, wo;
+  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  MPC_REQUIRE(X && W && A && B && C && Z, "null pointer");
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  const i64 nx = d->batch * d->c_in * d->h * d->w;
+  algo = resolve_algo(algo, M, N, K);
+  if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
+  const size_t need = conv_ws(P, *d, ho, wo, algo);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  u64* Ecol = cv.take(K * N);
+  u64* Acol[MPC_MAX_PARTIES];
+  for (int p = 0; p < P; ++p) Acol[p] = cv.take(K * N);
+  u64* F = cv.take(M * K);
+  u64* G = cv.take(M * K);
+  // E = sum_p (X_p - A_p) gathered straight into im2col layout.
+  if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)X, (const u64*)A, nx, P}, Ecol, s))
+    return rc;
+  for (int p = 0; p < P; ++p)
+    if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)A + p * nx, nullptr, nx, 1},
+                               Acol[p], s))
+      return rc;
+  MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
+  if (int rc = check_launch("open F")) return rc;
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.hw_out = ho * wo;
+  g.trunc_bits = trunc_bits;
+  g.njobs = P;
+  for (int p = 0; p < P; ++p) {
+    g.jobs[p].A1 = p == 0 ? G : (const u64*)B + (i64)p * M * K;
+    g.jobs[p].B1 = Ecol;
+    g.jobs[p].A2 = F;
+    g.jobs[p].B2 = Acol[p];
+    g.jobs[p].C = (const u64*)C + (i64)p * M * N;
+    g.jobs[p].Z = (u64*)Z + (i64)p * M * N;
+  }
+  int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s);
+  if (rc == MPC_OK)
+    stats_add(1, 8ull * (uint64_t)(nx + M * K), 0, (uint64_t)P * (nx + M * K + M * N),
+              (uint64_t)P * 2ull * M * N * K);
+  return rc;
+}
+
+size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo) {
+  if (M < 0 || N < 0 || K < 0) return 0;
+  return engine_ws(resolve_algo(algo, M, N, K), M, N, K, 1, 1);
+}
+
+int mpc_ring_gemm(int64_t M, int64_t N, int64_t K, const uint64_t* A, const uint64_t* B,
+                  const uint64_t* C, uint64_t* Z, int algo, void* ws, size_t ws_bytes,
+                  void* stream) {
+  if (int rc = check_algo(algo)) return rc;
+  MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
+  if (M == 0 || N == 0) return MPC_OK;
+  MPC_REQUIRE(A && B && Z, "null pointer");
+  algo = resolve_algo(algo, M, N, K);
+  if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support M=%lld N=%lld K=%lld",
+                (long long)M, (long long)N, (long long)K);
+  const size_t need = engine_ws(algo, M, N, K, 1, 1);
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.njobs = 1;
+  g.jobs[0] = GemmJob{(const u64*)A, (const u64*)B, nullptr, nullptr, (const u64*)C, (u64*)Z};
+  int rc = run_gemm(g, algo, ws, ws_bytes, as_stream(stream));
+  if (rc == MPC_OK) stats_add(0, 0, 0, 0, 2ull * M * N * K);
+  return rc;
+}
+
+size_t mpc_matmul_triple_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo) {
+  if (P < 1 || P > MPC_MAX_PARTIES || M < 0 || N < 0 || K < 0) return 0;
+  return matmul_triple_ws(M, N, K, resolve_algo(algo, M, N, K));
+}
+
+int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed, uint64_t op_id,
+                          uint64_t* A, uint64_t* B, uint64_t* C, int algo, void* ws,
+                          size_t ws_bytes, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  if (int rc = check_algo(algo)) return rc;
+  MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
+  MPC_REQUIRE(A && B && C, "null pointer");
+  algo = resolve_algo(algo, M, N, K);
+  if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this shape");
+  const size_t need = matmul_triple_ws(M, N, K, algo);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  u64* a = cv.take(M * K);
+  u64* b = cv.take(K * N);
+  if (M * K > 0) {
+    fill_sum_kernel<<<grid_for(ceil_div(M * K, 4), kThreads), kThreads, 0, s>>>(
+        P, M * K, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a);
+    if (int rc = check_launch("fill A")) return rc;
+  }
+  if (K * N > 0) {
+    fill_sum_kernel<<<grid_for(ceil_div(K * N, 4), kThreads), kThreads, 0, s>>>(
+        P, K * N, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b);
+    if (int rc = check_launch("fill B")) return rc;
+  }
+  if (M * N == 0) return MPC_OK;
+  u64* Clast = (u64*)C + (i64)(P - 1) * M * N;
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.njobs = 1;
+  g.jobs[0] = GemmJob{a, b, nullptr, nullptr, nullptr, Clast};
+  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s)) return rc;
+  share_product_kernel<<<grid_for(ceil_div(M * N, 4), kThreads), kThreads, 0, s>>>(
+      P, M * N, seed, op_id, (u64*)C);
+  return check_launch("share product");
+}
+
+size_t mpc_conv2d_triple_workspace_size(int P, const mpc_conv_desc* d, int algo) {
+  i64 ho, wo;
+  if (P < 1 || P > MPC_MAX_PARTIES || validate_conv(d, &ho, &wo) != MPC_OK) return 0;
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  return conv_triple_ws(*d, ho, wo, resolve_algo(algo, M, N, K));
+}
+
+int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t op_id,
+                          uint64_t* A, uint64_t* B, uint64_t* C, int algo, void* ws,
+                          size_t ws_bytes, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  if (int rc = check_algo(algo)) return rc;
+  i64 ho, wo;
+  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  MPC_REQUIRE(A && B && C, "null pointer");
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  const i64 nx = d->batch * d->c_in * d->h * d->w;
+  algo = resolve_algo(algo, M, N, K);
+  if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
+  const size_t need = conv_triple_ws(*d, ho, wo, algo);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  u64* a = cv.take(nx);
+  u64* acol = cv.take(K * N);
+  u64* b = cv.take(M * K);
+  fill_sum_kernel<<<grid_for(ceil_div(nx, 4), kThreads), kThreads, 0, s>>>(
+      P, nx, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a);
+  if (int rc = check_launch("fill A")) return rc;
+  fill_sum_kernel<<<grid_for(ceil_div(M * K, 4), kThreads), kThreads, 0, s>>>(
+      P, M * K, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b);
+  if (int rc = check_launch("fill B")) return rc;
+  if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{a, nullptr, 0, 1}, acol, s)) return rc;
+  u64* Clast = (u64*)C + (i64)(P - 1) * M * N;
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.hw_out = ho * wo;
+  g.njobs = 1;
+  g.jobs[0] = GemmJob{b, acol, nullptr, nullptr, nullptr, Clast};
+  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s)) return rc;
+  share_product_kernel<<<grid_for(ceil_div(M * N, 4), kThreads), kThreads, 0, s>>>(
+      P, M * N, seed, op_id, (u64*)C);
+  return check_launch("share product");
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared entry
+point, and rejects bad arguments on the host before touching a GPU.
+
+No compute entry point is called with valid arguments here (there is no GPU);
+every call below fails validation first, by construction of the ABI.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpc_ring.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_00984_b300 import build
+    build.build()
+    from paper_2109_00984_b300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["mpc_ring_share", "mpc_reveal", "mpc_beaver_mul", "mpc_beaver_matmul",
+                     "mpc_beaver_conv2d", "mpc_truncate", "mpc_a2b", "mpc_private_relu",
+                     "mpc_ttp_mul_triple", "mpc_ttp_matmul_triple", "mpc_ttp_conv2d_triple",
+                     "mpc_ttp_and_triples", "mpc_ttp_b2a_bits", "mpc_ring_gemm"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2109_00984_b300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} missing from the Python signature table"
+
+
+E = dict(OK=0, EINVAL=-1, ERANGE=-2, ENOMEM=-3, ECUDA=-4, ETIMEOUT=-5, EUNSUPPORTED=-6)
+NULL = None
+FAKE = ctypes.c_void_p(0x1000)   # never dereferenced: every call fails validation first
+
+
+def test_bad_party_counts_rejected(lib):
+    assert lib.mpc_beaver_mul(0, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
+    assert lib.mpc_beaver_mul(9, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
+    assert b"party count" in lib.mpc_last_error()
+    assert lib.mpc_ring_share(FAKE, 10, 2, 2, 16, 1, 1, FAKE, NULL) == E["EINVAL"]   # src >= P
+    assert lib.mpc_private_relu(3, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_a2b(1, 10, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
+
+
+def test_null_pointers_rejected(lib):
+    assert lib.mpc_beaver_mul(2, 10, FAKE, NULL, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
+    assert lib.mpc_reveal(FAKE, 2, 10, 16, NULL, NULL, NULL) == E["EINVAL"]
+    assert lib.mpc_private_relu(2, 10, FAKE, FAKE, NULL, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EINVAL"]
+
+
+def test_bad_sizes_rejected(lib):
+    assert lib.mpc_truncate(2, -1, FAKE, 16, 0, NULL) == E["EINVAL"]
+    assert lib.mpc_truncate(2, 10, FAKE, 64, 0, NULL) == E["EINVAL"]
+    assert lib.mpc_truncate(2, 10, FAKE, 16, -3, NULL) == E["EINVAL"]
+    assert lib.mpc_beaver_mul(2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 64, NULL) == E["EINVAL"]
+    assert lib.mpc_beaver_matmul(2, -1, 4, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 0, 0, FAKE, 1 << 20, NULL) == E["EINVAL"]
+    assert lib.mpc_ring_share(FAKE, 10, 2, 0, 63, 1, 1, FAKE, NULL) == E["EINVAL"]
+    assert lib.mpc_ttp_and_triples(2, 10, 0, 1, 1, FAKE, NULL) == E["EINVAL"]
+    assert lib.mpc_beaver_matmul(2, 4, 4, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 7, 0, FAKE, 1 << 20, NULL) == E["EINVAL"]
+
+
+def test_zero_length_is_a_no_op(lib):
+    assert lib.mpc_beaver_mul(2, 0, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, 0, NULL) == E["OK"]
+    assert lib.mpc_truncate(2, 0, NULL, 16, 0, NULL) == E["OK"]
+    assert lib.mpc_private_relu(2, 0, NULL, NULL, NULL, NULL, NULL, NULL, 1, 1, NULL) == E["OK"]
+
+
+def test_workspace_too_small_rejected(lib):
+    need = lib.mpc_matmul_workspace_size(2, 64, 32, 128, 0)
+    assert need >= 8 * (64 * 128 + 2 * 128 * 32)
+    rc = lib.mpc_beaver_matmul(2, 64, 32, 128, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 0, 16, FAKE,
+                               need - 1, NULL)
+    assert rc == E["ENOMEM"]
+    assert b"workspace" in lib.mpc_last_error()
+
+
+def test_conv_descriptor_validation(lib):
+    from paper_2109_00984_b300 import _lib
+    d = _lib.ConvDesc(1, 3, 5, 5, 4, 7, 7, 1, 1, 0, 0)   # kernel larger than input
+    assert lib.mpc_conv2d_workspace_size(2, ctypes.byref(d), 0) == 0
+    rc = lib.mpc_beaver_conv2d(2, ctypes.byref(d), FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 0, 16, FAKE,
+                               1 << 20, NULL)
+    assert rc == E["EINVAL"]
+    d2 = _lib.ConvDesc(1, 3, 5, 5, 4, 3, 3, 0, 1, 1, 1)  # zero stride
+    assert lib.mpc_beaver_conv2d(2, ctypes.byref(d2), FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 0, 16,
+                                 FAKE, 1 << 20, NULL) == E["EINVAL"]
+
+
+def test_stats_counters_reset(lib):
+    from paper_2109_00984_b300 import _lib
+    assert lib.mpc_reset_stats() == 0
+    s = _lib.Stats()
+    assert lib.mpc_get_stats(ctypes.byref(s)) == 0
+    assert s.calls == 0 and s.rounds == 0

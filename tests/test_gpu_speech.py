@@ -1,0 +1,62 @@
+"""The private speech-shaped conv stack on the GPU against the oracle, bit-exact.
+
+The reduced stack (3 layers, ragged lengths) checks every share of every
+layer's output; the full stack (80 -> 256 channels, 1600 frames, 7 layers: the
+workload bench.py times, in the same launch configuration) checks every share
+of the final output against the oracle's complete private forward, and the
+decoded output against float64 within the paper's NMSE bound (§6.1: < 4e-4).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import dev_f64, host  # noqa: E402
+
+import synth  # noqa: E402
+from oracle import nets  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mpc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_00984_b300 as m
+    return m
+
+
+def _run(mpc, x, ws, strides, pads, algo, step=0):
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+    sched = synth.speech_schedule(len(ws), step=step)
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=algo,
+                             weight_ops=sched["weight_op"], seed=sched["seed"])
+    Y = net.forward(dev_f64(x), sched)
+    real = net.reveal(Y)
+    torch.cuda.synchronize()
+    return host(Y), real.cpu().numpy(), sched
+
+
+def _oracle(x, ws, strides, pads, sched):
+    Wsh = nets.share_weights(ws, sched)
+    return nets.private_conv1d_stack(x, Wsh, strides, pads, sched, return_shares=True)
+
+
+@pytest.mark.parametrize("step", [0, 3])
+def test_small_stack_bit_exact(mpc, step):
+    x, ws, strides, pads = synth.speech_small()
+    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, mpc.PLAIN, step)
+    ref_real, ref_shares = _oracle(x, ws, strides, pads, sched)
+    assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
+    assert np.array_equal(got_real.reshape(ref_real.shape), ref_real)
+
+
+@pytest.mark.slow
+def test_full_speech_stack_bit_exact(mpc):
+    x, ws, strides, pads = synth.speech_stack()
+    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, mpc.PLAIN)
+    ref_real, ref_shares = _oracle(x, ws, strides, pads, sched)
+    assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
+    plain = nets.plaintext_conv1d_stack(x, ws, strides, pads)
+    nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
+    assert nmse < 4e-4
