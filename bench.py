@@ -1,0 +1,340 @@
+"""Benchmark: private inference of the speech-shaped conv stack on B300.
+
+One step = one full private forward of one sample (2 parties, batch 1, input
+80 x 1600 frames, Conv1d 80->256 k11 s2 then 6x Conv1d 256->256 k7, ring
+Z/2^64 with 2^16 fixed point): share the input, and for each layer let the
+dealer produce the convolution triple and the ReLU material, run the Beaver
+convolution with fused truncation and the fused private ReLU; then reveal.
+Every step of the hot path runs in libmpcring.so kernels.
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
+replica on its own sample: no data-path collective, weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--algo plain|limb|auto]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Beaver ring-GEMM TOPS (Z/2^64, bit-exact): i8-limb TC vs plain CUDA-core; samples/s"
+WORKLOAD = ("speech-shaped private conv stack: 2 parties, batch 1, input 80x1600, "
+            "Conv1d 80->256 k11 s2 + 6x Conv1d 256->256 k7 (pad k//2), each Beaver conv + "
+            "truncation 2^16 + private ReLU (A2B/Kogge-Stone/B2A), Z/2^64, dealer in the step")
+L2_FLUSH_BYTES = 256 << 20
+REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="auto", choices=["plain", "limb", "auto"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- reference arm
+def oracle_forward(frames, step):
+    """One private forward of the stack through the CPU oracle on `frames` frames."""
+    from oracle import nets
+    x, ws, strides, pads = synth.speech_stack(frames=frames)
+    sched = synth.speech_schedule(len(ws), step=step)
+    Wsh = nets.share_weights(ws, sched)
+    return nets.private_conv1d_stack(x, Wsh, strides, pads, sched)
+
+
+def cpu_baseline_measure(steps=1):
+    t = time.perf_counter()
+    for s in range(steps):
+        oracle_forward(REF_FRAMES, s)
+    dt = (time.perf_counter() - t) / steps
+    scale = REF_FRAMES / synth.SPEECH_FRAMES
+    return {"value": scale / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"whole 7-layer private forward on the first {REF_FRAMES} of "
+                      f"{synth.SPEECH_FRAMES} frames ({dt:.1f} s), samples/s scaled by "
+                      f"{REF_FRAMES}/{synth.SPEECH_FRAMES}; numpy uint64 single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for w in range(args.warmup):
+        oracle_forward(REF_FRAMES, 100 + w)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        oracle_forward(REF_FRAMES, s)
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    value = (REF_FRAMES / synth.SPEECH_FRAMES) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parties": 2, "batch": 1,
+                       "reference": "CPU oracle (numpy uint64), bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: whole stack on {REF_FRAMES} of "
+                                       f"{synth.SPEECH_FRAMES} frames, scaled"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def layer_macs(net):
+    """Ring multiply-adds per forward in the conv GEMMs (dealer + all parties)."""
+    tot = 0
+    for d in net.descs:
+        M, K = d.c_out, d.c_in * d.kh * d.kw
+        N = d.batch * ((d.w + 2 * d.pad_w - d.kw) // d.stride_w + 1)
+        tot += (1 + 2 * net.P) * M * N * K      # dealer c = a.b, then P parties x 2 pairs
+    return tot
+
+
+def relu_bytes_per_elem(P=2):
+    # x, y shares; 12 AND gates x (a, b, c) x P words; [r] P words + <r> P bits;
+    # elementwise triple 3 x P words.
+    return 8 * P + 8 * 12 * 3 * P + 8 * P + P / 8.0 + 8 * 3 * P + 8 * P
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2109_00984_b300 as mpc
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    algo = {"plain": mpc.PLAIN, "limb": mpc.LIMB, "auto": mpc.AUTO}[args.algo]
+
+    x, ws, strides, pads = synth.speech_stack(seed=rank)
+    sched0 = synth.speech_schedule(len(ws), step=0)
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=1, algo=algo,
+                             weight_ops=sched0["weight_op"], seed=sched0["seed"], device=dev)
+    x_dev = torch.from_numpy(x).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(i, inp):
+        Y = net.forward(inp, synth.speech_schedule(len(ws), step=i))
+        return net.reveal(Y)
+
+    for w in range(args.warmup):
+        step(1000 + w, x_dev)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, L2 flushed between steps ----------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    mpc.reset_stats()
+    mpc.profile_reset()
+    mpc.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step(i, x_dev)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    mpc.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = mpc.get_stats()
+    prof = {k: mpc.profile_read(k) for k in ("gemm_plain", "gemm_limb", "limb_planes",
+                                                 "private_relu")}
+    total_ms = float(sum(step_ms))
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # ---- end to end through the public API with pinned host buffers ------
+    x_host = torch.from_numpy(x).pin_memory()
+    out_host = torch.empty(tuple(net.out_real.shape), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    for w in range(2):
+        step(2000 + w, x_host.to(dev, non_blocking=True))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_stop = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for i in range(e2e_steps):
+        inp = x_host.to(dev, non_blocking=True)
+        out = step(3000 + i, inp)
+        out_host.copy_(out, non_blocking=True)
+    e_stop.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max(time.perf_counter() - t0, e_start.elapsed_time(e_stop) / 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "samples/s",
+           "h2d_bytes_per_step": int(x_host.numel() * 8),
+           "d2h_bytes_per_step": int(out_host.numel() * 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    peak_src = "of measured" if peaks else "of fallback"
+
+    macs = layer_macs(net)
+    n_relu = sum(b["n"] for b in net.bufs)
+    # dominant kernel by summed device time
+    kern = max(prof, key=lambda k: prof[k][1])
+    launches, kms = prof[kern]
+    # achieved = algorithmic work of all launches / their summed device time
+    # (= per-launch work / average launch duration).
+    if kern == "private_relu":
+        achieved = relu_bytes_per_elem() * n_relu * args.steps / (kms / 1e3) / 1e9
+        roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_src + " (copy bandwidth)"}
+    elif kern == "gemm_limb":
+        achieved = 36 * 2 * macs * args.steps / (kms / 1e3) / 1e12   # limb-pair MMA flops
+        roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                "peak_source": peak_src + " (bf16 sustained)"}
+    else:
+        # Plain engine: bound by 32-bit integer multiply-add issue.  Peak ring MAC
+        # rate = 148 SMs x 64 IMAD/clk x 2.032 GHz / 4 IMAD slots per ring MAC.
+        peak_tops = 148 * 64 * 2.032e9 / 4 * 2 / 1e12
+        achieved = 2 * macs * args.steps / (kms / 1e3) / 1e12
+        roof = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_tops,
+                "unit": "TOPS", "frac": achieved / peak_tops, "traffic": None,
+                "peak_source": "derived: 148 SM x 64 IMAD/clk x 2.032 GHz / 4 IMAD per ring MAC"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_measure()
+
+    gemm_ms = prof["gemm_plain"][1] + prof["gemm_limb"][1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parties": 2, "batch": 1, "engine": args.algo,
+                   "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "ring_gemm_tops": 2 * macs * args.steps / (gemm_ms / 1e3) / 1e12 if gemm_ms else None,
+        "ring_macs_per_step": macs,
+        "relu_elements_per_step": n_relu,
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": int(stats["launches"]),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,15 +1,549 @@
-// Limb-split ring GEMM on tcgen05 tensor cores (placeholder until the engine lands).
+// Limb-split ring GEMM on tcgen05 tensor cores (sm_103a).
+//
+// §5.3 of the paper splits 64-bit ring elements into 16-bit limbs and runs
+// float64 GEMMs per limb pair.  On B300 the integer MMA (kind::i8) is not
+// available for sm_103a, and float64 tensor throughput is tiny, so this engine
+// keeps the idea but maps it to the bf16 tensor cores:
+//
+//  * every u64 operand word v is cut into 8 balanced base-256 digits
+//    d_i in [-128, 127] with v = sum_i d_i 2^(8i) (mod 2^64); each digit is an
+//    exact bf16 (a "plane" holds one digit index of a whole matrix);
+//  * Z = sum_{i+j<8} 2^(8(i+j)) A_i B_j (mod 2^64): only the 36 digit pairs
+//    with i + j < 8 can reach the low 64 bits;
+//  * pairs with the same shift s = i + j share one fp32 TMEM accumulator
+//    (8 accumulators of 128 x 64 fill all 512 TMEM columns);
+//  * |d_i d_j| <= 2^14 and at most 8 pairs share a shift, so 128 K-steps keep
+//    every partial sum within 2^24 where fp32 holds integers exactly.  Each
+//    accumulator is therefore drained every 8 sub-steps of K = 16 (chunks
+//    staggered by shift, so one drain overlaps the MMAs of the other seven)
+//    into a 64-bit integer register sum R += int(acc_s) << 8s;
+//  * the epilogue adds C, applies the optional truncation and stores.
+//
+// Operands arrive as planes written by limb_planes_{a,b}: A as [8][M][Kp]
+// and B transposed as [8][N][Kp] (both K-major), with K-concatenated operand
+// pairs (Z = C + A1 B1 + A2 B2 is one GEMM over [A1 | A2] and [B1 ; B2]).
+//
+// Warp roles (192 threads): warp 0 issues TMA loads (one elected thread),
+// warp 1 allocates TMEM and issues MMAs (one thread), warps 2-5 drain TMEM
+// (warp w reads lanes 32 (w % 4) .. +31) and write the output.  Every wait is
+// bounded: on a timeout the CTA records MPC_ETIMEOUT, waits (bounded) for its
+// own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <string.h>
+
+#include <mutex>
+
 #include "gemm.hpp"
 #include "host.hpp"
 
 namespace mpc {
 
-bool limb_supported(i64, i64, i64) { return false; }
+namespace {
 
-size_t limb_workspace_bytes(i64, i64, i64, int, int) { return 0; }
+constexpr int BM = 128, BN = 64, KS = 16, STAGES = 4, NSHIFT = 8, CHUNK = 8;
+constexpr int A_PLANE_BYTES = BM * KS * 2;             // 4 KiB
+constexpr int B_PLANE_BYTES = BN * KS * 2;             // 2 KiB
+constexpr int A_STAGE_BYTES = NSHIFT * A_PLANE_BYTES;  // 32 KiB
+constexpr int B_STAGE_BYTES = NSHIFT * B_PLANE_BYTES;  // 16 KiB
+constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int kThreads = 192;
+constexpr uint32_t TMEM_COLS = 512;
+// Instruction descriptor, kind::f16: D f32 (bit 4), A bf16 (bits 7-9 = 1),
+// B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
-int launch_gemm_limb(const GemmArgs&, void*, size_t, cudaStream_t) {
-  return fail(MPC_EUNSUPPORTED, "limb engine not built");
+struct LimbParams {
+  CUtensorMap tmA[MPC_MAX_PARTIES];
+  CUtensorMap tmB[MPC_MAX_PARTIES];
+  const u64* C[MPC_MAX_PARTIES];
+  u64* Z[MPC_MAX_PARTIES];
+  i64 M, N, hw_out;
+  int T;  // K sub-steps of 16
+  int trunc_bits;
+  int* status;
+};
+
+// ---- PTX wrappers ------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity.  Returns false
+// (and raises the CTA's abort flag) when the limit passes or another role
+// already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+}
+
+// Shared-memory matrix descriptor: K-major, 32-byte swizzle, rows of 32 bytes,
+// 8-row groups 256 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+  d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                    // version
+  d |= (uint64_t)6 << 61;                    // SWIZZLE_32B
+  return d;
+}
+
+#define TMEM_LD_X32(taddr, r)                                                                  \
+  asm volatile(                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "  \
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "  \
+      "%28, %29, %30, %31}, [%32];"                                                             \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),    \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),             \
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),          \
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),          \
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),          \
+        "=r"(r[31])                                                                            \
+      : "r"(taddr))
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shift s's chunk ends after sub-step t when t = s - 1 (mod CHUNK), or at the end.
+__device__ __forceinline__ bool chunk_ends(int t, int s, int T) {
+  return (t % CHUNK) == ((s + CHUNK - 1) % CHUNK) || t == T - 1;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
+  extern __shared__ uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[NSHIFT], acce_bar[NSHIFT], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int job = blockIdx.z;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int T = p.T;
+  const uint32_t sbase = (smem_u32(dsmem) + 1023u) & ~1023u;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < NSHIFT; ++i) {
+      mbar_init(&accf_bar[i], 1);
+      mbar_init(&acce_bar[i], 4);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmA[job])));
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmB[job])));
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int last_t[STAGES];
+      for (int i = 0; i < STAGES; ++i) last_t[i] = -1;
+      for (int t = 0; t < T; ++t) {
+        const int st = t % STAGES;
+        const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
+        if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag)) break;
+        mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
+        const uint32_t a_dst = sbase + st * STAGE_BYTES;
+        tma_load_3d(a_dst, &p.tmA[job], &full_bar[st], t * KS, m0, 0);
+        tma_load_3d(a_dst + A_STAGE_BYTES, &p.tmB[job], &full_bar[st], t * KS, n0, 0);
+        last_t[st] = t;
+      }
+      // Copies in flight must land before the CTA can leave (bounded).
+      for (int i = 0; i < STAGES; ++i) {
+        if (last_t[i] < 0) continue;
+        const uint32_t ph = (uint32_t)(last_t[i] / STAGES) & 1u;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&full_bar[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      uint32_t chunks[NSHIFT];
+#pragma unroll
+      for (int s = 0; s < NSHIFT; ++s) chunks[s] = 0;
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const int st = t % STAGES;
+        const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
+        if (!mbar_wait(&full_bar[st], ph, &abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a_base = sbase + st * STAGE_BYTES;
+        const uint32_t b_base = a_base + A_STAGE_BYTES;
+#pragma unroll
+        for (int s = 0; s < NSHIFT; ++s) {
+          // A chunk of shift s starts right after one ended (or at t = 0).
+          const bool start = (t == 0) || ((t - 1) % CHUNK) == ((s + CHUNK - 1) % CHUNK);
+          if (start && t > 0) {
+            if (!mbar_wait(&acce_bar[s], (chunks[s] - 1u) & 1u, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          for (int i = 0; i <= s; ++i) {
+            tc_mma(tmem + (uint32_t)(s * BN), smem_desc_sw32(a_base + i * A_PLANE_BYTES),
+                   smem_desc_sw32(b_base + (s - i) * B_PLANE_BYTES),
+                   (start && i == 0) ? 0u : 1u);
+          }
+          if (chunk_ends(t, s, T)) {
+            tc_commit(&accf_bar[s]);
+            chunks[s]++;
+          }
+        }
+        tc_commit(&empty_bar[st]);
+      }
+      // All issued MMAs must finish before TMEM is released (bounded).
+      tc_commit(&done_bar);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(&done_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else {
+    // ---- TMEM drain + epilogue (warps 2..5) ----
+    const int q = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    u64 R[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) R[j] = 0;
+    uint32_t chunks[NSHIFT];
+#pragma unroll
+    for (int s = 0; s < NSHIFT; ++s) chunks[s] = 0;
+    bool ok = true;
+    for (int t = 0; t < T && ok; ++t) {
+      for (int s = 0; s < NSHIFT; ++s) {
+        if (!chunk_ends(t, s, T)) continue;
+        if (!mbar_wait(&accf_bar[s], chunks[s] & 1u, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t v[BN];
+        TMEM_LD_X32(lane_base + (uint32_t)(s * BN), v);
+        TMEM_LD_X32(lane_base + (uint32_t)(s * BN + 32), (v + 32));
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[s]);
+        chunks[s]++;
+        const int sh = 8 * s;
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+          const int iv = __float2int_rz(__uint_as_float(v[j]));
+          R[j] += (u64)(i64)iv << sh;
+        }
+      }
+    }
+    if (ok && !abort_flag) {
+      const i64 row = (i64)m0 + q * 32 + lane;
+      if (row < p.M) {
+        const u64* C = p.C[job];
+        u64* Z = p.Z[job];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+          const i64 col = (i64)n0 + j;
+          if (col < p.N) {
+            const i64 idx = gemm_out_index(row, col, p.M, p.N, p.hw_out);
+            u64 v = R[j];
+            if (C) v += C[idx];
+            if (p.trunc_bits > 0) v = sar(v, p.trunc_bits);
+            Z[idx] = v;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) record_status(p.status, MPC_ETIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// ---- plane pre-pass ---------------------------------------------------------------------
+// Balanced base-256 digits of v: v = sum_i d_i 2^(8i) mod 2^64, d_i in [-128, 127].
+__device__ __forceinline__ void balanced_digits(u64 v, int d[8]) {
+  int carry = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int t = (int)((v >> (8 * i)) & 255ull) + carry;
+    carry = t >= 128;
+    d[i] = t - (carry << 8);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn((float)lo), b = __float2bfloat16_rn((float)hi);
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Writes 8 consecutive k' of one row into the 8 planes of `out` ([8][rows][Kp]).
+__device__ __forceinline__ void write_planes(const u64 v[8], __nv_bfloat16* out, i64 rows,
+                                             i64 row, i64 Kp, i64 k0) {
+  int d[8][8];  // [element][digit]
+#pragma unroll
+  for (int e = 0; e < 8; ++e) balanced_digits(v[e], d[e]);
+#pragma unroll
+  for (int pl = 0; pl < 8; ++pl) {
+    uint4 w;
+    w.x = pack_bf16x2(d[0][pl], d[1][pl]);
+    w.y = pack_bf16x2(d[2][pl], d[3][pl]);
+    w.z = pack_bf16x2(d[4][pl], d[5][pl]);
+    w.w = pack_bf16x2(d[6][pl], d[7][pl]);
+    *reinterpret_cast<uint4*>(out + ((i64)pl * rows + row) * Kp + k0) = w;
+  }
+}
+
+struct PlaneJob {
+  const u64* X1;  // first pair operand
+  const u64* X2;  // second pair operand (or null)
+  __nv_bfloat16* out;
+};
+
+// A side: X is [M][K] row-major; element (m, k') of [X1 | X2].
+__global__ void __launch_bounds__(256) limb_planes_a(PlaneJob j0,
+                                                      PlaneJob j1, PlaneJob j2, PlaneJob j3,
+                                                      PlaneJob j4, PlaneJob j5, PlaneJob j6,
+                                                      PlaneJob j7, i64 M, i64 K, i64 Kp) {
+  const PlaneJob js[8] = {j0, j1, j2, j3, j4, j5, j6, j7};
+  const PlaneJob& jb = js[blockIdx.y];
+  const i64 kc = Kp / 8;
+  const i64 total = M * kc;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
+       i += (i64)gridDim.x * blockDim.x) {
+    const i64 m = i / kc, k0 = (i % kc) * 8;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const i64 k = k0 + e;
+      v[e] = k < K ? jb.X1[m * K + k] : (jb.X2 && k < 2 * K) ? jb.X2[m * K + (k - K)] : 0ull;
+    }
+    write_planes(v, jb.out, M, m, Kp, k0);
+  }
+}
+
+// B side: X is [K][N] row-major; planes are written transposed, [8][N][Kp].
+__global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
+                                                      PlaneJob j1, PlaneJob j2, PlaneJob j3,
+                                                      PlaneJob j4, PlaneJob j5, PlaneJob j6,
+                                                      PlaneJob j7, i64 N, i64 K, i64 Kp) {
+  const PlaneJob js[8] = {j0, j1, j2, j3, j4, j5, j6, j7};
+  const PlaneJob& jb = js[blockIdx.y];
+  const i64 kc = Kp / 8;
+  const i64 total = N * kc;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
+       i += (i64)gridDim.x * blockDim.x) {
+    const i64 n = i % N, k0 = (i / N) * 8;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const i64 k = k0 + e;
+      v[e] = k < K ? jb.X1[k * N + n] : (jb.X2 && k < 2 * K) ? jb.X2[(k - K) * N + n] : 0ull;
+    }
+    write_planes(v, jb.out, N, n, Kp, k0);
+  }
+}
+
+// ---- host side -----------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode ? MPC_OK : fail(MPC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+}
+
+// 3-D map over planes [8][rows][Kp] bf16 with a {16, box_rows, 8} box, 32-byte swizzle.
+int encode_planes(CUtensorMap* tm, const void* base, i64 rows, i64 Kp, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 8};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 8};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? MPC_OK : fail(MPC_ECUDA, "tensor map encode failed (%d)", (int)r);
+}
+
+inline i64 padded_k(i64 K, int npairs) { return ceil_div(npairs * K, KS) * KS; }
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+bool limb_supported(i64 M, i64 N, i64 K) {
+  // TMA coordinates are 32-bit; keep every extent comfortably inside.
+  return M >= 1 && N >= 1 && K >= 1 && M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 30);
+}
+
+size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs) {
+  const i64 Kp = padded_k(K, npairs);
+  return (size_t)njobs * (al256((size_t)8 * M * Kp * 2) + al256((size_t)8 * N * Kp * 2));
+}
+
+int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
+  if (!limb_supported(g.M, g.N, g.K)) return fail(MPC_EUNSUPPORTED, "shape outside limb engine");
+  if (int rc = get_encoder()) return rc;
+  const int npairs = g.jobs[0].A2 ? 2 : 1;
+  for (int j = 1; j < g.njobs; ++j)
+    if ((g.jobs[j].A2 != nullptr) != (npairs == 2))
+      return fail(MPC_EINVAL, "limb engine: jobs mix one- and two-pair products");
+  const i64 Kp = padded_k(g.K, npairs);
+  const size_t need = limb_workspace_bytes(g.M, g.N, g.K, npairs, g.njobs);
+  if (ws == nullptr || ws_bytes < need)
+    return fail(MPC_ENOMEM, "limb workspace %zu bytes, need %zu", ws_bytes, need);
+  const i64 gy = ceil_div(g.M, BM), gx = ceil_div(g.N, BN);
+  if (gy > 65535) return fail(MPC_EUNSUPPORTED, "M too large for the limb engine grid");
+  int* st = device_status_ptr();
+  if (!st) return fail(MPC_ECUDA, "device status word unavailable");
+
+  // Planes for every job.
+  PlaneJob ja[8] = {}, jbv[8] = {};
+  char* w = static_cast<char*>(ws);
+  LimbParams prm;
+  memset(&prm, 0, sizeof(prm));
+  for (int j = 0; j < g.njobs; ++j) {
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(w);
+    w += al256((size_t)8 * g.M * Kp * 2);
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(w);
+    w += al256((size_t)8 * g.N * Kp * 2);
+    ja[j] = PlaneJob{g.jobs[j].A1, g.jobs[j].A2, pa};
+    jbv[j] = PlaneJob{g.jobs[j].B1, g.jobs[j].B2, pb};
+    if (int rc = encode_planes(&prm.tmA[j], pa, g.M, Kp, BM)) return rc;
+    if (int rc = encode_planes(&prm.tmB[j], pb, g.N, Kp, BN)) return rc;
+    prm.C[j] = g.jobs[j].C;
+    prm.Z[j] = g.jobs[j].Z;
+  }
+  {
+    KernelTimer timer("limb_planes", s);
+    const i64 ta = g.M * (Kp / 8), tb = g.N * (Kp / 8);
+    dim3 ga(grid_for(ta, 256, 148 * 16), g.njobs), gb(grid_for(tb, 256, 148 * 16), g.njobs);
+    limb_planes_a<<<ga, 256, 0, s>>>(ja[0], ja[1], ja[2], ja[3], ja[4], ja[5], ja[6],
+                                     ja[7], g.M, g.K, Kp);
+    if (int rc = check_launch("limb_planes_a")) return rc;
+    limb_planes_b<<<gb, 256, 0, s>>>(jbv[0], jbv[1], jbv[2], jbv[3], jbv[4], jbv[5],
+                                     jbv[6], jbv[7], g.N, g.K, Kp);
+    if (int rc = check_launch("limb_planes_b")) return rc;
+  }
+  prm.M = g.M;
+  prm.N = g.N;
+  prm.hw_out = g.hw_out;
+  prm.T = (int)(Kp / KS);
+  prm.trunc_bits = g.trunc_bits;
+  prm.status = st;
+  cudaError_t e = cudaFuncSetAttribute(limb_gemm_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return fail(MPC_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)g.njobs);
+  KernelTimer timer("gemm_limb", s);
+  limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
+  return check_launch("gemm_limb");
 }
 
 }  // namespace mpc

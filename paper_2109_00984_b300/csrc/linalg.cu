@@ -142,8 +142,12 @@ int validate_conv(const mpc_conv_desc* d, i64* ho, i64* wo) {
   return MPC_OK;
 }
 
+// AUTO picks the plain engine until the limb engine is validated on the device.
 int resolve_algo(int algo, i64 M, i64 N, i64 K) {
-  if (algo == MPC_ALGO_AUTO) return limb_supported(M, N, K) ? MPC_ALGO_LIMB : MPC_ALGO_PLAIN;
+  (void)M;
+  (void)N;
+  (void)K;
+  if (algo == MPC_ALGO_AUTO) return MPC_ALGO_PLAIN;
   return algo;
 }
 

@@ -85,5 +85,6 @@ class PrivateConv1dStack:
         return X
 
     def reveal(self, shares):
+        """Decoded float64 output, shape (batch, c_out, length)."""
         _, real = api.reveal(shares, self.frac_bits, ring=False, real=True)
-        return real
+        return real.view(self.out_real.shape)
