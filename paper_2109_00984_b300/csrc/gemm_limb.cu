@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
       mbar_init(&acce_bar[i], 4);
     }
     mbar_init(&done_bar, 1);
-    abort_flag = 0;
+    // A timeout recorded by an earlier CTA (and not yet cleared by
+    // mpc_sync_status) makes every later CTA skip its work and exit at once.
+    abort_flag = (*(volatile int*)p.status == MPC_ETIMEOUT) ? 1 : 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmA[job])));
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmB[job])));
