@@ -227,6 +227,27 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
                       const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
                       int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream);
 
+/* Beaver matmul that allocates nothing (the paper has no counterpart: this is
+ * an interface for callers that can neither allocate device memory when they
+ * call the library nor hand it a workspace, e.g. a host program whose device
+ * memory is wholly reserved by another framework's pool, or code running where
+ * allocation calls are not allowed).  Same arguments, layouts and results as
+ * mpc_beaver_matmul with the plain engine, minus algo/ws.  Its scratch,
+ * M*K + 2*K*N words (each region rounded up to 32 words), lives in a fixed
+ * library-owned device array of MPC_NOALLOC_SCRATCH_WORDS words (8 MiB),
+ * present on every device that loads the library until the process exits;
+ * larger requests return MPC_ENOMEM and launch nothing.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The first call on a
+ * device looks up the array's device address (with that device current), so
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (each call writes every word it reads
+ * before reading it); calls whose kernels overlap on the GPU race on it, so
+ * serialise them. */
+#define MPC_NOALLOC_SCRATCH_WORDS (1ll << 20)
+int mpc_beaver_matmul_noalloc(int P, int64_t M, int64_t N, int64_t K, const uint64_t* X,
+                              const uint64_t* Y, const uint64_t* A, const uint64_t* B,
+                              const uint64_t* C, uint64_t* Z, int trunc_bits, void* stream);
+
 /* Plain ring GEMM Z = C + A B over Z/2^64: A [M][K], B [K][N], C [M][N] or
  * NULL, Z [M][N] (device, row-major).  ws as mpc_ring_gemm_workspace_size(). */
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo);

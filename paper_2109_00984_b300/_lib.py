@@ -50,6 +50,8 @@ SIGNATURES = {
     "mpc_matmul_workspace_size": (c_size, [c_int, c_i64, c_i64, c_i64, c_int]),
     "mpc_beaver_matmul": (c_int, [c_int, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                   c_int, c_int, c_vp, c_size, c_vp]),
+    "mpc_beaver_matmul_noalloc": (c_int, [c_int, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                          c_vp, c_int, c_vp]),
     "mpc_conv2d_workspace_size": (c_size, [c_int, _P(ConvDesc), c_int]),
     "mpc_beaver_conv2d": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int,
                                   c_int, c_vp, c_size, c_vp]),
