@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["plain", "limb", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="speech", choices=["speech", "gemm", "batched"],
+                    help="speech: the private conv stack (default); gemm: ring GEMM sweep; "
+                         "batched: 512 uneven Beaver matmuls")
+    ap.add_argument("--sizes", default="1024,2048,4096,8192")
     return ap.parse_args()
 
 
@@ -328,10 +332,171 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_gemm_sweep(args):
+    """Ring GEMM Z = A B over Z/2^64, M = N = K = n, words uniform over the ring.
+
+    Times each engine with CUDA events (L2 flushed between launches) and reports
+    ring TOPS = 2 n^3 / t; for the limb engine also the tensor-pipe rate
+    72 n^3 / t (36 bf16 digit-pair products per ring MAC) against the bf16 peak.
+    """
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    algos = {"plain": [mpc.PLAIN], "limb": [mpc.LIMB], "auto": [mpc.PLAIN, mpc.LIMB]}[args.algo]
+    out = {}
+    for n in [int(v) for v in args.sizes.split(",")]:
+        rng = np.random.default_rng(0)
+        A = torch.from_numpy(rng.integers(0, 2 ** 64, (n, n), dtype=np.uint64).view(np.int64)).to(dev)
+        B = torch.from_numpy(rng.integers(0, 2 ** 64, (n, n), dtype=np.uint64).view(np.int64)).to(dev)
+        Z = torch.empty((n, n), dtype=torch.int64, device=dev)
+        for algo in algos:
+            name = "limb" if algo == mpc.LIMB else "plain"
+            ws = torch.empty(max(1, mpc.ring_gemm_workspace_size(n, n, n, algo)), dtype=torch.uint8,
+                             device=dev)
+            reps = max(1, min(args.steps, int(2e12 // (n ** 3)) + 1))
+            mpc.ring_gemm(A, B, None, algo=algo, out=Z, ws=ws)
+            torch.cuda.synchronize()
+            mpc.profile_reset()
+            mpc.profile_enable(True)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mpc.ring_gemm(A, B, None, algo=algo, out=Z, ws=ws)
+                e1.record()
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            mpc.profile_enable(False)
+            ms = float(np.median([a.elapsed_time(b) for a, b in ts]))
+            rec = {"ms": ms, "ring_tops": 2 * n ** 3 / (ms / 1e3) / 1e12, "reps": reps}
+            if algo == mpc.LIMB:
+                kl, kms = mpc.profile_read("gemm_limb")
+                pl, pms = mpc.profile_read("limb_planes")
+                rec["mma_kernel_ms"] = kms / max(kl, 1)
+                rec["planes_ms"] = pms / max(pl, 1)
+                tf = 72 * n ** 3 / (rec["mma_kernel_ms"] / 1e3) / 1e12
+                rec["tensor_tflops"] = tf
+                rec["tensor_frac_of_bf16_burst"] = tf / bf16
+            out[f"{name}_{n}"] = rec
+            del ws
+        del A, B, Z
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "ring GEMM sweep M=N=K, uniform Z/2^64 words",
+                      "bf16_peak_tflops": bf16, "results": out}), flush=True)
+
+
+def run_batched(args):
+    """512 two-party Beaver matmuls with (M, N, K) log-uniform in [32, 2048] (seed 2).
+
+    Times the online step (opening + products + truncation; triples dealt
+    beforehand) three ways with CUDA events, L2 flushed between repetitions:
+    one beaver_matmul call per product, one batched call, and the batched call
+    captured once in a CUDA graph and replayed.
+    """
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P = 2
+    dims = synth.batched_dims()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    prods = []
+    for i, (M, N, K) in enumerate(dims):
+        M, N, K = int(M), int(N), int(K)
+        X = torch.randint(-2 ** 63, 2 ** 63 - 1, (P, M, K), dtype=torch.int64, device=dev, generator=gen)
+        Y = torch.randint(-2 ** 63, 2 ** 63 - 1, (P, K, N), dtype=torch.int64, device=dev, generator=gen)
+        A, B, C = mpc.ttp_matmul_triple(P, M, N, K, 1, 10000 + i, algo=mpc.AUTO, device=dev)
+        Z = torch.empty((P, M, N), dtype=torch.int64, device=dev)
+        prods.append((X, Y, A, B, C, Z))
+    ring_ops = float(sum(2 * P * 2 * int(M) * int(N) * int(K) for M, N, K in dims))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+    # (a) one call per product (the engine AUTO picks per shape)
+    ws = {}
+
+    def per_product():
+        for (X, Y, A, B, C, Z) in prods:
+            key = (X.shape, Y.shape)
+            w = ws.get(key)
+            if w is None:
+                M, K = X.shape[1], X.shape[2]
+                w = ws[key] = torch.empty(max(1, mpc.matmul_workspace_size(P, M, Y.shape[2], K, mpc.AUTO)),
+                                          dtype=torch.uint8, device=dev)
+            mpc.beaver_matmul(X, Y, A, B, C, algo=mpc.AUTO, trunc_bits=16, out=Z, ws=w)
+
+    per_product()
+    reps = max(3, min(args.steps, 10))
+    t_each = timed(per_product, reps)
+
+    # (b) one batched call, autotuned routing
+    bm = mpc.BatchedMatmul(prods, algo=mpc.AUTO, trunc_bits=16)
+    tune = bm.autotune()
+    bm.ensure_workspace(dev)
+    bm()
+    mpc.reset_stats()
+    t_batched = timed(bm, reps)
+    launches = mpc.get_stats()["launches"] / reps
+
+    # (c) the batched call captured in a CUDA graph
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            bm()
+    torch.cuda.synchronize()
+    g.replay()
+    t_graph = timed(g.replay, reps)
+
+    line = {"workload": "512 uneven 2-party Beaver matmuls, (M,N,K) log-uniform in [32,2048] "
+                        "(seed 2), truncation 2^16, online step (triples dealt beforehand)",
+            "ring_ops_per_batch": ring_ops,
+            "per_product_ms": t_each, "batched_ms": t_batched, "graph_ms": t_graph,
+            "per_product_ring_tops": ring_ops / (t_each / 1e3) / 1e12,
+            "batched_ring_tops": ring_ops / (t_batched / 1e3) / 1e12,
+            "graph_ring_tops": ring_ops / (t_graph / 1e3) / 1e12,
+            "speedup_graph_vs_per_product": t_each / t_graph,
+            "tuned_limb_min_macs": tune.limb_min_macs,
+            "kernel_launches_per_batched_call": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batched" and args.impl != "reference":
+        run_batched(args)
+        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "gemm":
+        run_gemm_sweep(args)
     else:
         run_ours(args)
 

@@ -248,6 +248,55 @@ int mpc_beaver_matmul_noalloc(int P, int64_t M, int64_t N, int64_t K, const uint
                               const uint64_t* Y, const uint64_t* A, const uint64_t* B,
                               const uint64_t* C, uint64_t* Z, int trunc_bits, void* stream);
 
+/* ---- batched Beaver matmul ----------------------------------------------- */
+
+/* One product of a batch: X [P][M][K], Y [P][K][N], triple A [P][M][K],
+ * B [P][K][N], C [P][M][N] and output Z [P][M][N], all device pointers. */
+typedef struct {
+  int64_t M, N, K;
+  const uint64_t* X;
+  const uint64_t* Y;
+  const uint64_t* A;
+  const uint64_t* B;
+  const uint64_t* C;
+  uint64_t* Z;
+} mpc_matmul_desc;
+
+/* Tuning of the batched call: products with M*N*K >= limb_min_macs run on the
+ * limb engine (algo AUTO); persistent_ctas = CTAs of the persistent plain
+ * kernel (0 = one per SM). */
+typedef struct {
+  double limb_min_macs;
+  int persistent_ctas;
+  int reserved;
+} mpc_tune;
+
+/* Fills the built-in tuning (limb from 2^28 ring MACs up). */
+int mpc_tune_default(mpc_tune* out);
+
+/* Batched Beaver matmul (App. D.1.1 applied to many products at once): every
+ * product is opened in one pass (one round for the whole batch), then the
+ * products below the limb threshold run in one persistent launch of the plain
+ * engine that hands out output tiles of any product from an atomic counter
+ * (largest K first), and the others on the limb engine.  Results equal
+ * mpc_beaver_matmul on each product.  descs: host array of `count`
+ * descriptors (read during the call only).  tune may be NULL (defaults).
+ * ws: device workspace of mpc_matmul_batched_workspace_size() bytes (it holds
+ * the work table, every product's opened E, F and B_0 + F, and limb
+ * scratch).  Stream-capturable: the descriptors reach the device as kernel
+ * parameters. */
+size_t mpc_matmul_batched_workspace_size(int P, int count, const mpc_matmul_desc* descs, int algo,
+                                         const mpc_tune* tune);
+int mpc_beaver_matmul_batched(int P, int count, const mpc_matmul_desc* descs, int algo,
+                              const mpc_tune* tune, int trunc_bits, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Autotuner: times the batched call (algo AUTO) for limb thresholds from
+ * "never" down to 2^20 ring MACs and returns the fastest in *out.
+ * Synchronises `stream`; not for use inside stream capture.  Writes Z. */
+int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int trunc_bits,
+                         void* ws, size_t ws_bytes, void* stream, mpc_tune* out);
+
 /* Plain ring GEMM Z = C + A B over Z/2^64: A [M][K], B [K][N], C [M][N] or
  * NULL, Z [M][N] (device, row-major).  ws as mpc_ring_gemm_workspace_size(). */
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo);

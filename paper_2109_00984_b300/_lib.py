@@ -24,6 +24,16 @@ class Stats(ctypes.Structure):
         "calls", "rounds", "bytes_opened", "and_gates", "triple_words", "ring_macs", "launches")]
 
 
+class MatmulDesc(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64)] + \
+        [(n, ctypes.c_void_p) for n in ("X", "Y", "A", "B", "C", "Z")]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("limb_min_macs", ctypes.c_double), ("persistent_ctas", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
 _P = ctypes.POINTER
 SIGNATURES = {
     "mpc_last_error": (ctypes.c_char_p, []),
@@ -55,6 +65,12 @@ SIGNATURES = {
     "mpc_conv2d_workspace_size": (c_size, [c_int, _P(ConvDesc), c_int]),
     "mpc_beaver_conv2d": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int,
                                   c_int, c_vp, c_size, c_vp]),
+    "mpc_tune_default": (c_int, [_P(Tune)]),
+    "mpc_matmul_batched_workspace_size": (c_size, [c_int, c_int, _P(MatmulDesc), c_int, _P(Tune)]),
+    "mpc_beaver_matmul_batched": (c_int, [c_int, c_int, _P(MatmulDesc), c_int, _P(Tune), c_int,
+                                          c_vp, c_size, c_vp]),
+    "mpc_autotune_batched": (c_int, [c_int, c_int, _P(MatmulDesc), c_int, c_vp, c_size, c_vp,
+                                     _P(Tune)]),
     "mpc_ring_gemm_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_int]),
     "mpc_ring_gemm": (c_int, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp, c_size,
                               c_vp]),

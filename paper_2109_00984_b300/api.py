@@ -245,6 +245,81 @@ def ring_gemm_workspace_size(M, N, K, algo=PLAIN):
     return int(_L().mpc_ring_gemm_workspace_size(M, N, K, algo))
 
 
+# ---- batched Beaver matmul -----------------------------------------------------------
+class BatchedMatmul:
+    """Marshalled argument set of mpc_beaver_matmul_batched for a fixed batch.
+
+    products: list of (X, Y, A, B, C, Z) CUDA tensors, X [P, M, K], Y [P, K, N],
+    A/B/C the Beaver triple, Z the output [P, M, N].  The descriptor array is
+    built once, so repeated calls (and a CUDA graph capture of a call) do no
+    per-product Python work.
+    """
+
+    def __init__(self, products, algo=AUTO, trunc_bits=16, tune=None):
+        self.P = products[0][0].shape[0]
+        self.count = len(products)
+        self.descs = (_lib.MatmulDesc * self.count)()
+        for i, (X, Y, A, B, C, Z) in enumerate(products):
+            P, M, K = X.shape
+            N = Y.shape[2]
+            assert P == self.P and Z.shape == (P, M, N)
+            self.descs[i] = _lib.MatmulDesc(M, N, K, *[ctypes.c_void_p(t.data_ptr()) for t in (
+                X, Y, A, B, C, Z)])
+            for t in (X, Y, A, B, C, Z):
+                _ptr(t)
+        self.products = products          # keep the tensors alive
+        self.algo = algo
+        self.trunc_bits = trunc_bits
+        self.tune = tune if tune is not None else default_tune()
+        self.ws = None
+
+    def workspace_size(self):
+        return int(_L().mpc_matmul_batched_workspace_size(self.P, self.count, self.descs, self.algo,
+                                                          ctypes.byref(self.tune)))
+
+    def ensure_workspace(self, device="cuda"):
+        need = self.workspace_size()
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = _ws(need, device)
+        return self.ws
+
+    def __call__(self):
+        ws = self.ensure_workspace(self.products[0][0].device)
+        _check(_L().mpc_beaver_matmul_batched(self.P, self.count, self.descs, self.algo,
+                                              ctypes.byref(self.tune), self.trunc_bits,
+                                              _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+
+    def autotune(self, ws_bytes=None):
+        """Pick the limb threshold by timing the call (synchronises; writes Z)."""
+        dev = self.products[0][0].device
+        if ws_bytes is None:
+            everything = _lib.Tune(1.0, 0, 0)    # the largest plan: every product on limb
+            ws_bytes = int(_L().mpc_matmul_batched_workspace_size(
+                self.P, self.count, self.descs, LIMB, ctypes.byref(everything)))
+        ws = _ws(ws_bytes, dev)
+        out = _lib.Tune()
+        _check(_L().mpc_autotune_batched(self.P, self.count, self.descs, self.trunc_bits,
+                                         _ptr(ws, "ws", torch.uint8), ws.numel(), _stream(),
+                                         ctypes.byref(out)))
+        self.tune = out
+        self.algo = AUTO
+        self.ws = None
+        return out
+
+
+def default_tune():
+    t = _lib.Tune()
+    _check(_L().mpc_tune_default(ctypes.byref(t)))
+    return t
+
+
+def beaver_matmul_batched(products, algo=AUTO, trunc_bits=16, tune=None):
+    """One call of mpc_beaver_matmul_batched over `products` (see BatchedMatmul)."""
+    bm = BatchedMatmul(products, algo, trunc_bits, tune)
+    bm()
+    return bm
+
+
 def truncate(shares, frac_bits=16, divisor=0):
     """In place on [P, ...] shares; returns shares."""
     P = shares.shape[0]

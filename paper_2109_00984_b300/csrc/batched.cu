@@ -1,0 +1,294 @@
+// Batched Beaver matmul: many products of uneven shapes in one call.
+//
+// Every product is opened in one batched kernel (one communication round for
+// the whole batch: all epsilons and deltas are revealed together, App. D.1.1),
+// then the products below the tuning threshold run in ONE persistent launch of
+// the plain engine, whose CTAs claim output tiles of any product from an
+// atomic counter (largest K first); products above it run on the tensor-core
+// limb engine.  The per-product descriptors reach the device through kernel
+// parameters (small table-writing kernels), so the whole call is
+// stream-capturable: a CUDA graph of it replays without host involvement.
+#include <algorithm>
+#include <vector>
+
+#include "gemm.hpp"
+#include "host.hpp"
+
+namespace mpc {
+
+namespace {
+
+constexpr int kTablePerLaunch = 48;  // 48 x 128-byte products per parameter block
+
+struct TableChunk {
+  BatchProd items[kTablePerLaunch];
+  int count;
+  int offset;
+};
+
+__global__ void table_write_kernel(const TableChunk chunk, BatchProd* tbl) {
+  const int i = threadIdx.x;
+  if (i < chunk.count) tbl[chunk.offset + i] = chunk.items[i];
+}
+
+// E = sum_p (X_p - A_p) for every product, F = sum_p (Y_p - B_p), G = B_0 + F.
+__global__ void __launch_bounds__(256) batched_open_kernel(const BatchProd* __restrict__ tbl,
+                                                           int count, int P, i64 total) {
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < total;
+       e += (i64)gridDim.x * blockDim.x) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tbl[mid].open_base <= e) lo = mid; else hi = mid - 1;
+    }
+    const BatchProd& b = tbl[lo];
+    i64 l = e - b.open_base;
+    const i64 mk = b.M * b.K;
+    if (l < mk) {
+      u64 v = 0;
+      for (int p = 0; p < P; ++p) v += b.X[p * mk + l] - b.A[p * mk + l];
+      b.E[l] = v;
+    } else {
+      l -= mk;
+      const i64 kn = b.K * b.N;
+      u64 v = 0;
+      for (int p = 0; p < P; ++p) v += b.Y[p * kn + l] - b.B[p * kn + l];
+      b.F[l] = v;
+      b.G[l] = b.B[l] + v;
+    }
+  }
+}
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Plan {
+  std::vector<int> order;  // products in table order: plain ones (K descending), then limb
+  int n_plain = 0;
+  size_t table_off = 0, efg_off = 0, limb_off = 0, total = 0;
+  size_t limb_bytes = 0;
+};
+
+bool use_limb(const mpc_matmul_desc& d, int algo, const mpc_tune& tune) {
+  if (algo == MPC_ALGO_PLAIN) return false;
+  if (!limb_supported(d.M, d.N, d.K)) return false;
+  if (algo == MPC_ALGO_LIMB) return true;
+  return (double)d.M * d.N * d.K >= tune.limb_min_macs;
+}
+
+int validate(int P, int count, const mpc_matmul_desc* descs, int algo) {
+  MPC_CHECK_PARTIES(P);
+  MPC_REQUIRE(count >= 0 && count <= (1 << 20), "product count %d outside [0, 2^20]", count);
+  MPC_REQUIRE(count == 0 || descs != nullptr, "null descriptor array");
+  MPC_REQUIRE(algo == MPC_ALGO_PLAIN || algo == MPC_ALGO_LIMB || algo == MPC_ALGO_AUTO,
+              "unknown algo %d", algo);
+  for (int i = 0; i < count; ++i) {
+    const mpc_matmul_desc& d = descs[i];
+    MPC_REQUIRE(d.M >= 1 && d.N >= 1 && d.K >= 1, "product %d: dimensions must be >= 1", i);
+    MPC_REQUIRE(d.M <= (1ll << 31) && d.N <= (1ll << 31) && d.K <= (1ll << 31),
+                "product %d: dimension too large", i);
+    MPC_REQUIRE(d.X && d.Y && d.A && d.B && d.C && d.Z, "product %d: null pointer", i);
+  }
+  return MPC_OK;
+}
+
+Plan make_plan(int P, int count, const mpc_matmul_desc* descs, int algo, const mpc_tune& tune) {
+  Plan pl;
+  std::vector<int> plain, limb;
+  for (int i = 0; i < count; ++i) (use_limb(descs[i], algo, tune) ? limb : plain).push_back(i);
+  std::stable_sort(plain.begin(), plain.end(),
+                   [&](int a, int b) { return descs[a].K > descs[b].K; });
+  pl.order = plain;
+  pl.order.insert(pl.order.end(), limb.begin(), limb.end());
+  pl.n_plain = (int)plain.size();
+  size_t off = 256;  // work counter
+  pl.table_off = off;
+  off += al256((size_t)count * sizeof(BatchProd));
+  pl.efg_off = off;
+  for (int i = 0; i < count; ++i) {
+    const mpc_matmul_desc& d = descs[i];
+    off += al256((size_t)d.M * d.K * 8) + 2 * al256((size_t)d.K * d.N * 8);
+  }
+  pl.limb_off = off;
+  for (int i : limb)
+    pl.limb_bytes =
+        std::max(pl.limb_bytes, engine_ws(MPC_ALGO_LIMB, descs[i].M, descs[i].N, descs[i].K, 2, P));
+  pl.total = off + al256(pl.limb_bytes);
+  return pl;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return kPlanSMs;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return kPlanSMs;
+  return n;
+}
+
+int run_batched(int P, int count, const mpc_matmul_desc* descs, int algo, const mpc_tune& tune,
+                int trunc_bits, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (count == 0) return MPC_OK;
+  const Plan pl = make_plan(P, count, descs, algo, tune);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < pl.total)
+    return fail(MPC_ENOMEM, "batched workspace %zu bytes, need %zu", ws_bytes, pl.total);
+  char* base = static_cast<char*>(ws);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(base);
+  BatchProd* tbl = reinterpret_cast<BatchProd*>(base + pl.table_off);
+
+  // Host copy of the table, in processing order.
+  std::vector<BatchProd> h(count);
+  size_t efg = pl.efg_off;
+  i64 tile_base = 0, open_base = 0;
+  for (int j = 0; j < count; ++j) {
+    const mpc_matmul_desc& d = descs[pl.order[j]];
+    BatchProd& b = h[j];
+    b.M = d.M;
+    b.N = d.N;
+    b.K = d.K;
+    i64 tm, tn;
+    plain_tiles(d.M, d.N, &tm, &tn);
+    b.tiles_m = (int)tm;
+    b.tiles_n = (int)tn;
+    b.tile_base = tile_base;
+    b.tiles = j < pl.n_plain ? (i64)P * tm * tn : 0;
+    tile_base += b.tiles;
+    b.open_base = open_base;
+    open_base += d.M * d.K + d.K * d.N;
+    b.X = (const u64*)d.X;
+    b.Y = (const u64*)d.Y;
+    b.A = (const u64*)d.A;
+    b.B = (const u64*)d.B;
+    b.C = (const u64*)d.C;
+    b.Z = (u64*)d.Z;
+    b.E = reinterpret_cast<u64*>(base + efg);
+    efg += al256((size_t)d.M * d.K * 8);
+    b.F = reinterpret_cast<u64*>(base + efg);
+    efg += al256((size_t)d.K * d.N * 8);
+    b.G = reinterpret_cast<u64*>(base + efg);
+    efg += al256((size_t)d.K * d.N * 8);
+  }
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return fail(MPC_ECUDA, "counter reset: %s", cudaGetErrorString(e));
+  for (int off = 0; off < count; off += kTablePerLaunch) {
+    TableChunk ch;
+    ch.count = std::min(kTablePerLaunch, count - off);
+    ch.offset = off;
+    for (int i = 0; i < ch.count; ++i) ch.items[i] = h[off + i];
+    table_write_kernel<<<1, kTablePerLaunch, 0, s>>>(ch, tbl);
+    if (int rc = check_launch("batched table")) return rc;
+  }
+  batched_open_kernel<<<grid_for(open_base, 256), 256, 0, s>>>(tbl, count, P, open_base);
+  if (int rc = check_launch("batched open")) return rc;
+  if (pl.n_plain > 0) {
+    const int ctas = tune.persistent_ctas > 0 ? tune.persistent_ctas : sm_count();
+    if (int rc = launch_gemm_plain_batched(tbl, pl.n_plain, P, trunc_bits, counter, ctas, s))
+      return rc;
+  }
+  for (int j = pl.n_plain; j < count; ++j) {
+    const BatchProd& b = h[j];
+    GemmArgs g{};
+    g.M = b.M;
+    g.N = b.N;
+    g.K = b.K;
+    g.trunc_bits = trunc_bits;
+    g.njobs = P;
+    for (int p = 0; p < P; ++p) {
+      g.jobs[p].A1 = b.E;
+      g.jobs[p].B1 = p == 0 ? b.G : b.B + (i64)p * b.K * b.N;
+      g.jobs[p].A2 = b.A + (i64)p * b.M * b.K;
+      g.jobs[p].B2 = b.F;
+      g.jobs[p].C = b.C + (i64)p * b.M * b.N;
+      g.jobs[p].Z = b.Z + (i64)p * b.M * b.N;
+    }
+    if (int rc = run_gemm(g, MPC_ALGO_LIMB, base + pl.limb_off, pl.limb_bytes, s)) return rc;
+  }
+  uint64_t opened = 0, macs = 0;
+  for (int i = 0; i < count; ++i) {
+    opened += 8ull * (descs[i].M * descs[i].K + descs[i].K * descs[i].N);
+    macs += (uint64_t)P * 2ull * descs[i].M * descs[i].N * descs[i].K;
+  }
+  stats_add(1, opened, 0, 0, macs);
+  return MPC_OK;
+}
+
+mpc_tune default_tune() {
+  mpc_tune t;
+  t.limb_min_macs = 268435456.0;  // 2^28 ring MACs per party-GEMM
+  t.persistent_ctas = 0;
+  t.reserved = 0;
+  return t;
+}
+
+}  // namespace
+
+}  // namespace mpc
+
+using namespace mpc;
+
+extern "C" {
+
+int mpc_tune_default(mpc_tune* out) {
+  MPC_REQUIRE(out != nullptr, "null tune pointer");
+  *out = default_tune();
+  return MPC_OK;
+}
+
+size_t mpc_matmul_batched_workspace_size(int P, int count, const mpc_matmul_desc* descs, int algo,
+                                         const mpc_tune* tune) {
+  if (validate(P, count, descs, algo) != MPC_OK) return 0;
+  const mpc_tune t = tune ? *tune : default_tune();
+  return make_plan(P, count, descs, algo, t).total;
+}
+
+int mpc_beaver_matmul_batched(int P, int count, const mpc_matmul_desc* descs, int algo,
+                              const mpc_tune* tune, int trunc_bits, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (int rc = validate(P, count, descs, algo)) return rc;
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  const mpc_tune t = tune ? *tune : default_tune();
+  return run_batched(P, count, descs, algo, t, trunc_bits, ws, ws_bytes, as_stream(stream));
+}
+
+int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int trunc_bits,
+                         void* ws, size_t ws_bytes, void* stream, mpc_tune* out) {
+  if (int rc = validate(P, count, descs, MPC_ALGO_AUTO)) return rc;
+  MPC_REQUIRE(out != nullptr, "null tune pointer");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(MPC_ECUDA, "event creation failed");
+  mpc_tune best = default_tune();
+  float best_ms = -1.f;
+  // Candidate thresholds: everything plain, then 2^32 down to 2^20 ring MACs.
+  std::vector<double> cands = {1e300};
+  for (int lg = 32; lg >= 20; lg -= 2) cands.push_back((double)(1ull << lg));
+  int rc = MPC_OK;
+  for (double c : cands) {
+    mpc_tune t = default_tune();
+    t.limb_min_macs = c;
+    if (make_plan(P, count, descs, MPC_ALGO_AUTO, t).total > ws_bytes) continue;
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 3 && rc == MPC_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = run_batched(P, count, descs, MPC_ALGO_AUTO, t, trunc_bits, ws, ws_bytes, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(MPC_ECUDA, "autotune sync failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;  // the first run warms up
+    }
+    if (rc != MPC_OK) break;
+    if (best_ms < 0.f || ms_sum < best_ms) {
+      best_ms = ms_sum;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MPC_OK) return rc;
+  if (best_ms < 0.f) return fail(MPC_ENOMEM, "workspace too small for every candidate");
+  *out = best;
+  return MPC_OK;
+}
+
+}  // extern "C"

@@ -20,13 +20,35 @@ struct GemmJob {
   u64* Z;
 };
 
+// splits > 1 partitions the (pair-concatenated) K range over `splits` CTAs per
+// output tile; each writes its raw partial sum to partial[split][job][M][N]
+// and gemm_reduce() forms Z = trunc(C + sum of partials) (exact mod 2^64).
 struct GemmArgs {
   i64 M, N, K;
   i64 hw_out;
   int trunc_bits;
   int njobs;
+  int splits;
+  u64* partial;
   GemmJob jobs[MPC_MAX_PARTIES];
 };
+
+// Number of SMs the split heuristics plan for (B300).
+constexpr int kPlanSMs = 148;
+
+// Split count minimising waves x K-units per CTA for `tiles` output tiles and
+// `units` K-units (each at least `min_units` per split).
+int choose_splits(i64 tiles, i64 units, i64 min_units);
+
+// Per-engine split choice (deterministic in the shape) and partial-sum bytes.
+int plain_splits(i64 M, i64 N, i64 K, int npairs, int njobs);
+int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs);
+inline size_t partial_bytes(int splits, int njobs, i64 M, i64 N) {
+  return splits > 1 ? (size_t)splits * njobs * M * N * sizeof(u64) : 0;
+}
+
+// Z[job] = trunc(C[job] + sum_s partial[s][job]) with the output scatter.
+int gemm_reduce(const GemmArgs& g, cudaStream_t s);
 
 __host__ __device__ __forceinline__ i64 gemm_out_index(i64 row, i64 col, i64 M, i64 N,
                                                        i64 hw_out) {
@@ -36,10 +58,36 @@ __host__ __device__ __forceinline__ i64 gemm_out_index(i64 row, i64 col, i64 M, 
 // Engines: each returns MPC_OK or an mpc_status with the error message set.
 int launch_gemm_plain(const GemmArgs& g, cudaStream_t s);
 
-// Limb engine (tcgen05).  ws/ws_bytes: caller workspace; limb_workspace_bytes
-// tells how much it needs for the given shape and job count.
+// One product of a batched Beaver matmul, as stored in device memory.  Per
+// party p the plain engine computes Z_p = C_p + E (B_p or G for p = 0) + A_p F.
+struct BatchProd {
+  i64 M, N, K;
+  i64 tile_base;  // first work item of this product (prefix over the batch)
+  i64 tiles;      // P * tiles_m * tiles_n
+  i64 open_base;  // first element of this product in the batched opening
+  int tiles_m, tiles_n;
+  const u64 *X, *Y, *A, *B, *C;
+  u64* Z;
+  u64 *E, *F, *G;  // opened E [M][K], F [K][N], G = B_0 + F (workspace)
+};
+
+// Persistent plain engine over the products of `tbl` (device); `counter`
+// (device, zeroed by the caller) hands out work items.
+int launch_gemm_plain_batched(const BatchProd* tbl, int count, int P, int trunc_bits,
+                              unsigned long long* counter, int ctas, cudaStream_t s);
+int plain_tiles(i64 M, i64 N, i64* tm, i64* tn);
+
+// Limb engine (tcgen05).  ws/ws_bytes: caller workspace (digit planes);
+// limb_workspace_bytes tells how much it needs for the given shape and job
+// count.  Partial sums for split-K live in g.partial (sized by the caller).
 size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs);
 int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t s);
 bool limb_supported(i64 M, i64 N, i64 K);
+
+// Engine dispatch shared by the entry points: split choice, workspace bytes
+// (split-K partials, then limb planes) and the launch of one GEMM job set.
+int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
+size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
+int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s);
 
 }  // namespace mpc

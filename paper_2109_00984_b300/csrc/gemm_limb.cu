@@ -23,9 +23,12 @@
 // and B transposed as [8][N][Kp] (both K-major), with K-concatenated operand
 // pairs (Z = C + A1 B1 + A2 B2 is one GEMM over [A1 | A2] and [B1 ; B2]).
 //
-// Warp roles (192 threads): warp 0 issues TMA loads (one elected thread),
-// warp 1 allocates TMEM and issues MMAs (one thread), warps 2-5 drain TMEM
-// (warp w reads lanes 32 (w % 4) .. +31) and write the output.  Every wait is
+// Warp roles (416 threads): warp 0 issues TMA loads (one thread); warps 1-4
+// each issue the MMAs of two shifts, {w, 7 - w}, 9 per K sub-step (one thread
+// per warp: a single issuing thread cannot keep the tensor pipe busy with
+// N = 64 MMAs); warp 1 also allocates TMEM; warps 5-12 drain TMEM, two per
+// lane quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each, and
+// write the output.  Every wait is
 // bounded: on a timeout the CTA records MPC_ETIMEOUT, waits (bounded) for its
 // own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -50,7 +53,9 @@ constexpr int A_STAGE_BYTES = NSHIFT * A_PLANE_BYTES;  // 32 KiB
 constexpr int B_STAGE_BYTES = NSHIFT * B_PLANE_BYTES;  // 16 KiB
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int kThreads = 192;
+constexpr int kIssuers = 4;      // MMA-issuing warps (1..4)
+constexpr int kDrainWarps = 8;   // TMEM drain / epilogue warps (5..12)
+constexpr int kThreads = 32 * (1 + kIssuers + kDrainWarps);
 constexpr uint32_t TMEM_COLS = 512;
 // Instruction descriptor, kind::f16: D f32 (bit 4), A bf16 (bits 7-9 = 1),
 // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -63,9 +68,11 @@ struct LimbParams {
   CUtensorMap tmB[MPC_MAX_PARTIES];
   const u64* C[MPC_MAX_PARTIES];
   u64* Z[MPC_MAX_PARTIES];
+  u64* partial;  // split-K partial sums [splits][njobs][M][N] (splits > 1)
   i64 M, N, hw_out;
   int T;  // K sub-steps of 16
   int trunc_bits;
+  int splits, njobs;
   int* status;
 };
 
@@ -181,9 +188,61 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shift s's chunk ends after sub-step t when t = s - 1 (mod CHUNK), or at the end.
-__device__ __forceinline__ bool chunk_ends(int t, int s, int T) {
-  return (t % CHUNK) == ((s + CHUNK - 1) % CHUNK) || t == T - 1;
+// The s + 1 digit-pair MMAs of shift S: D += sum_{i <= S} A_i B_{S - i}.
+template <int S>
+__device__ __forceinline__ void issue_shift_t(uint32_t d, uint64_t a0, uint64_t b0, bool start) {
+  tc_mma(d, a0, b0 + (uint64_t)(S * (B_PLANE_BYTES >> 4)), start ? 0u : 1u);
+#pragma unroll
+  for (int i = 1; i <= S; ++i)
+    tc_mma(d, a0 + (uint64_t)(i * (A_PLANE_BYTES >> 4)),
+           b0 + (uint64_t)((S - i) * (B_PLANE_BYTES >> 4)), 1u);
+}
+
+// Shift s's chunk ends after sub-step t when t = s - 1 (mod CHUNK), or at the
+// end t_end - 1 of the CTA's K range.
+__device__ __forceinline__ bool chunk_ends(int t, int s, int t_end) {
+  return (t % CHUNK) == ((s + CHUNK - 1) % CHUNK) || t == t_end - 1;
+}
+
+// The two shifts owned by MMA-issuer warp w: {w, 7 - w}, 9 digit-pair MMAs
+// per K sub-step for every issuer.
+template <int W>
+__device__ __forceinline__ void issuer_loop(const LimbParams& p, uint32_t sbase, uint32_t tmem,
+                                            int t_begin, int t_end, uint64_t* full_bar,
+                                            uint64_t* empty_bar, uint64_t* accf_bar,
+                                            uint64_t* acce_bar, volatile int* abort_flag) {
+  constexpr int S0 = W, S1 = NSHIFT - 1 - W;
+  uint32_t chunks0 = 0, chunks1 = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    const int st = (t - t_begin) % STAGES;
+    const uint32_t ph = (uint32_t)((t - t_begin) / STAGES) & 1u;
+    if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
+    tc_fence_after();
+    const uint64_t a0 = smem_desc_sw32(sbase + st * STAGE_BYTES);
+    const uint64_t b0 = smem_desc_sw32(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
+    // A chunk of shift s starts right after one ended (or at t = t_begin).
+    const bool start0 = (t == t_begin) || ((t - 1) % CHUNK) == ((S0 + CHUNK - 1) % CHUNK);
+    const bool start1 = (t == t_begin) || ((t - 1) % CHUNK) == ((S1 + CHUNK - 1) % CHUNK);
+    if (start0 && t > t_begin) {
+      if (!mbar_wait(&acce_bar[S0], (chunks0 - 1u) & 1u, abort_flag)) return;
+      tc_fence_after();
+    }
+    issue_shift_t<S0>(tmem + (uint32_t)(S0 * BN), a0, b0, start0);
+    if (chunk_ends(t, S0, t_end)) {
+      tc_commit(&accf_bar[S0]);
+      chunks0++;
+    }
+    if (start1 && t > t_begin) {
+      if (!mbar_wait(&acce_bar[S1], (chunks1 - 1u) & 1u, abort_flag)) return;
+      tc_fence_after();
+    }
+    issue_shift_t<S1>(tmem + (uint32_t)(S1 * BN), a0, b0, start1);
+    if (chunk_ends(t, S1, t_end)) {
+      tc_commit(&accf_bar[S1]);
+      chunks1++;
+    }
+    tc_commit(&empty_bar[st]);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
@@ -194,21 +253,23 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int job = blockIdx.z;
+  const int job = blockIdx.z / p.splits, split = blockIdx.z % p.splits;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int T = p.T;
+  // This CTA's K sub-steps [t_begin, t_end).
+  const int t_begin = (int)((i64)p.T * split / p.splits);
+  const int t_end = (int)((i64)p.T * (split + 1) / p.splits);
   const uint32_t sbase = (smem_u32(dsmem) + 1023u) & ~1023u;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], 1);
+      mbar_init(&empty_bar[i], kIssuers);
     }
     for (int i = 0; i < NSHIFT; ++i) {
       mbar_init(&accf_bar[i], 1);
-      mbar_init(&acce_bar[i], 4);
+      mbar_init(&acce_bar[i], kDrainWarps);
     }
-    mbar_init(&done_bar, 1);
+    mbar_init(&done_bar, kIssuers);
     // A timeout recorded by an earlier CTA (and not yet cleared by
     // mpc_sync_status) makes every later CTA skip its work and exit at once.
     abort_flag = (*(volatile int*)p.status == MPC_ETIMEOUT) ? 1 : 0;
@@ -232,15 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
       // ---- TMA producer ----
       int last_t[STAGES];
       for (int i = 0; i < STAGES; ++i) last_t[i] = -1;
-      for (int t = 0; t < T; ++t) {
-        const int st = t % STAGES;
-        const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
+      for (int t = t_begin; t < t_end; ++t) {
+        const int st = (t - t_begin) % STAGES;
+        const uint32_t ph = (uint32_t)((t - t_begin) / STAGES) & 1u;
         if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag)) break;
         mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
         const uint32_t a_dst = sbase + st * STAGE_BYTES;
         tma_load_3d(a_dst, &p.tmA[job], &full_bar[st], t * KS, m0, 0);
         tma_load_3d(a_dst + A_STAGE_BYTES, &p.tmB[job], &full_bar[st], t * KS, n0, 0);
-        last_t[st] = t;
+        last_t[st] = t - t_begin;
       }
       // Copies in flight must land before the CTA can leave (bounded).
       for (int i = 0; i < STAGES; ++i) {
@@ -251,71 +312,48 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp <= kIssuers) {
     if (lane == 0) {
-      // ---- MMA issuer ----
-      uint32_t chunks[NSHIFT];
-#pragma unroll
-      for (int s = 0; s < NSHIFT; ++s) chunks[s] = 0;
-      bool ok = true;
-      for (int t = 0; t < T && ok; ++t) {
-        const int st = t % STAGES;
-        const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
-        if (!mbar_wait(&full_bar[st], ph, &abort_flag)) break;
-        tc_fence_after();
-        const uint32_t a_base = sbase + st * STAGE_BYTES;
-        const uint32_t b_base = a_base + A_STAGE_BYTES;
-#pragma unroll
-        for (int s = 0; s < NSHIFT; ++s) {
-          // A chunk of shift s starts right after one ended (or at t = 0).
-          const bool start = (t == 0) || ((t - 1) % CHUNK) == ((s + CHUNK - 1) % CHUNK);
-          if (start && t > 0) {
-            if (!mbar_wait(&acce_bar[s], (chunks[s] - 1u) & 1u, &abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          for (int i = 0; i <= s; ++i) {
-            tc_mma(tmem + (uint32_t)(s * BN), smem_desc_sw32(a_base + i * A_PLANE_BYTES),
-                   smem_desc_sw32(b_base + (s - i) * B_PLANE_BYTES),
-                   (start && i == 0) ? 0u : 1u);
-          }
-          if (chunk_ends(t, s, T)) {
-            tc_commit(&accf_bar[s]);
-            chunks[s]++;
-          }
-        }
-        tc_commit(&empty_bar[st]);
+      // ---- MMA issuers: warp 1 + w owns shifts {w, 7 - w} ----
+      switch (warp - 1) {
+        case 0: issuer_loop<0>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
+                               acce_bar, &abort_flag); break;
+        case 1: issuer_loop<1>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
+                               acce_bar, &abort_flag); break;
+        case 2: issuer_loop<2>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
+                               acce_bar, &abort_flag); break;
+        default: issuer_loop<3>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
+                                acce_bar, &abort_flag); break;
       }
-      // All issued MMAs must finish before TMEM is released (bounded).
+      // All of this issuer's MMAs must finish before TMEM is released (bounded).
       tc_commit(&done_bar);
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(&done_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
       }
     }
   } else {
-    // ---- TMEM drain + epilogue (warps 2..5) ----
-    const int q = warp & 3;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    u64 R[BN];
+    // ---- TMEM drain + epilogue: 8 warps, two per TMEM lane quadrant ----
+    const int ew = warp - 1 - kIssuers;           // 0..7
+    const int q = warp & 3;                       // lane quadrant this warp may access
+    const int half = ew >> 2;                     // which 32 of the 64 columns
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    u64 R[32];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) R[j] = 0;
+    for (int j = 0; j < 32; ++j) R[j] = 0;
     uint32_t chunks[NSHIFT];
 #pragma unroll
     for (int s = 0; s < NSHIFT; ++s) chunks[s] = 0;
     bool ok = true;
-    for (int t = 0; t < T && ok; ++t) {
+    for (int t = t_begin; t < t_end && ok; ++t) {
       for (int s = 0; s < NSHIFT; ++s) {
-        if (!chunk_ends(t, s, T)) continue;
+        if (!chunk_ends(t, s, t_end)) continue;
         if (!mbar_wait(&accf_bar[s], chunks[s] & 1u, &abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        uint32_t v[BN];
+        uint32_t v[32];
         TMEM_LD_X32(lane_base + (uint32_t)(s * BN), v);
-        TMEM_LD_X32(lane_base + (uint32_t)(s * BN + 32), (v + 32));
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
@@ -323,20 +361,26 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
         chunks[s]++;
         const int sh = 8 * s;
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
+        for (int j = 0; j < 32; ++j) {
           const int iv = __float2int_rz(__uint_as_float(v[j]));
           R[j] += (u64)(i64)iv << sh;
         }
       }
     }
-    if (ok && !abort_flag) {
-      const i64 row = (i64)m0 + q * 32 + lane;
-      if (row < p.M) {
+    const i64 row = (i64)m0 + q * 32 + lane;
+    const int c0 = n0 + half * 32;
+    if (ok && !abort_flag && row < p.M) {
+      if (p.splits > 1) {
+        u64* part = p.partial + ((i64)split * p.njobs + job) * p.M * p.N + row * p.N;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if ((i64)c0 + j < p.N) part[c0 + j] = R[j];
+      } else {
         const u64* C = p.C[job];
         u64* Z = p.Z[job];
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          const i64 col = (i64)n0 + j;
+        for (int j = 0; j < 32; ++j) {
+          const i64 col = (i64)c0 + j;
           if (col < p.N) {
             const i64 idx = gemm_out_index(row, col, p.M, p.N, p.hw_out);
             u64 v = R[j];
@@ -478,6 +522,11 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
+int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs) {
+  const i64 tiles = ceil_div(M, BM) * ceil_div(N, BN) * njobs;
+  return choose_splits(tiles, padded_k(K, npairs) / KS, 32);
+}
+
 bool limb_supported(i64 M, i64 N, i64 K) {
   // TMA coordinates are 32-bit; keep every extent comfortably inside.
   return M >= 1 && N >= 1 && K >= 1 && M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 30);
@@ -488,8 +537,12 @@ size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs) {
   return (size_t)njobs * (al256((size_t)8 * M * Kp * 2) + al256((size_t)8 * N * Kp * 2));
 }
 
-int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t s) {
+int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream_t s) {
+  GemmArgs g = g_in;
+  if (g.splits < 1) g.splits = 1;
   if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
+  if ((g.splits > 1 && g.partial == nullptr) || g.splits * g.njobs > 65535)
+    return fail(MPC_EINVAL, "bad split configuration");
   if (!limb_supported(g.M, g.N, g.K)) return fail(MPC_EUNSUPPORTED, "shape outside limb engine");
   if (int rc = get_encoder()) return rc;
   const int npairs = g.jobs[0].A2 ? 2 : 1;
@@ -538,14 +591,20 @@ int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t 
   prm.hw_out = g.hw_out;
   prm.T = (int)(Kp / KS);
   prm.trunc_bits = g.trunc_bits;
+  prm.splits = g.splits;
+  prm.njobs = g.njobs;
+  prm.partial = g.partial;
   prm.status = st;
   cudaError_t e = cudaFuncSetAttribute(limb_gemm_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return fail(MPC_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)g.njobs);
-  KernelTimer timer("gemm_limb", s);
-  limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
-  return check_launch("gemm_limb");
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(g.njobs * g.splits));
+  {
+    KernelTimer timer("gemm_limb", s);
+    limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
+    if (int rc = check_launch("gemm_limb")) return rc;
+  }
+  return g.splits > 1 ? gemm_reduce(g, s) : MPC_OK;
 }
 
 }  // namespace mpc

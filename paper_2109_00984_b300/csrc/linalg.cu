@@ -142,26 +142,46 @@ int validate_conv(const mpc_conv_desc* d, i64* ho, i64* wo) {
   return MPC_OK;
 }
 
-// AUTO picks the plain engine until the limb engine is validated on the device.
+// AUTO: the tensor-core limb engine from about a million ring MACs up (it is
+// 3-4x faster than the plain engine from 1024^3 on); the plain engine below,
+// where launch and plane pre-pass costs dominate.
 int resolve_algo(int algo, i64 M, i64 N, i64 K) {
-  (void)M;
-  (void)N;
-  (void)K;
-  if (algo == MPC_ALGO_AUTO) return MPC_ALGO_PLAIN;
-  return algo;
-}
-
-int run_gemm(const GemmArgs& g, int algo, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (algo == MPC_ALGO_LIMB) return launch_gemm_limb(g, ws, ws_bytes, s);
-  return launch_gemm_plain(g, s);
-}
-
-size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
-  return algo == MPC_ALGO_LIMB ? limb_workspace_bytes(M, N, K, npairs, njobs) : 0;
+  if (algo != MPC_ALGO_AUTO) return algo;
+  return (limb_supported(M, N, K) && (double)M * N * K >= 1048576.0) ? MPC_ALGO_LIMB
+                                                                     : MPC_ALGO_PLAIN;
 }
 
 inline size_t words(i64 n) { return (size_t)n * sizeof(u64); }
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
+  return algo == MPC_ALGO_LIMB ? limb_splits(M, N, K, npairs, njobs)
+                               : plain_splits(M, N, K, npairs, njobs);
+}
+
+// Engine workspace: split-K partial sums, then (limb) the digit planes.
+size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
+  const int sp = engine_splits(algo, M, N, K, npairs, njobs);
+  size_t b = align256(partial_bytes(sp, njobs, M, N));
+  if (algo == MPC_ALGO_LIMB) b += limb_workspace_bytes(M, N, K, npairs, njobs);
+  return b;
+}
+
+int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
+  const int npairs = g.jobs[0].A2 ? 2 : 1;
+  g.splits = engine_splits(algo, g.M, g.N, g.K, npairs, g.njobs);
+  const size_t pb = align256(partial_bytes(g.splits, g.njobs, g.M, g.N));
+  if (ws_bytes < pb) return fail(MPC_ENOMEM, "engine workspace too small for split-K partials");
+  g.partial = g.splits > 1 ? static_cast<u64*>(ws) : nullptr;
+  void* rest = static_cast<char*>(ws) + pb;
+  if (algo == MPC_ALGO_LIMB) return launch_gemm_limb(g, rest, ws_bytes - pb, s);
+  return launch_gemm_plain(g, s);
+}
+
+namespace {
 
 // Workspace carving (each region 256-byte aligned).
 struct Carve {

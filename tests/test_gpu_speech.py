@@ -51,12 +51,23 @@ def test_small_stack_bit_exact(mpc, step):
     assert np.array_equal(got_real.reshape(ref_real.shape), ref_real)
 
 
-@pytest.mark.slow
-def test_full_speech_stack_bit_exact(mpc):
+@pytest.fixture(scope="module")
+def full_oracle():
     x, ws, strides, pads = synth.speech_stack()
-    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, mpc.PLAIN)
+    sched = synth.speech_schedule(len(ws))
     ref_real, ref_shares = _oracle(x, ws, strides, pads, sched)
-    assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     plain = nets.plaintext_conv1d_stack(x, ws, strides, pads)
+    return ref_shares, plain
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("engine", ["plain", "auto"])
+def test_full_speech_stack_bit_exact(mpc, full_oracle, engine):
+    """Full stack in bench.py's configuration (engine AUTO = limb for these shapes)."""
+    x, ws, strides, pads = synth.speech_stack()
+    algo = mpc.PLAIN if engine == "plain" else mpc.AUTO
+    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, algo)
+    ref_shares, plain = full_oracle
+    assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
     assert nmse < 4e-4
