@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["plain", "limb", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="speech", choices=["speech", "gemm", "batched"],
+    ap.add_argument("--workload", default="speech", choices=["speech", "gemm", "batched", "resnet"],
                     help="speech: the private conv stack (default); gemm: ring GEMM sweep; "
                          "batched: 512 uneven Beaver matmuls")
     ap.add_argument("--sizes", default="1024,2048,4096,8192")
@@ -488,8 +488,62 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_resnet(args):
+    """Private inference of the ResNet-18-shaped CNN: 2 parties, batch 8 of 3x224x224.
+
+    One step = share the batch, deal and consume all material of every layer
+    (convolutions, ReLUs, max-pool tree, residual adds, average pool, FC),
+    reveal the logits.  Device-timed with CUDA events, L2 flushed between steps.
+    """
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+    from paper_2109_00984_b300.resnet import PrivateResNet18
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    batch = 8
+    x = torch.from_numpy(synth.resnet_input(batch=batch, hw=224)).to(dev)
+    sched = synth.resnet_schedule()
+    net = PrivateResNet18(synth.resnet_weights(), synth.RESNET18, sched, algo=mpc.AUTO, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    for w in range(max(1, args.warmup)):
+        net.reveal(net.forward(x, synth.resnet_schedule(step=100 + w)))
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    mpc.profile_reset()
+    mpc.profile_enable(True)
+    mpc.reset_stats()
+    ts = []
+    for i in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.reveal(net.forward(x, synth.resnet_schedule(step=i)))
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    mpc.profile_enable(False)
+    ms = float(sum(a.elapsed_time(b) for a, b in ts)) / steps
+    prof = {k: mpc.profile_read(k) for k in ("gemm_plain", "gemm_limb", "limb_planes",
+                                                 "private_relu", "gemm_plain_batched")}
+    stats = mpc.get_stats()
+    line = {"workload": "private ResNet-18-shaped inference, 2 parties, batch 8 x 3x224x224, "
+                        "He-init weights, dealer in the step",
+            "value": batch / (ms / 1e3), "unit": "images/s", "ms_per_step": ms, "steps": steps,
+            "paper_context_images_per_s": 1 / 2.49,
+            "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0]},
+            "ring_macs_per_step": stats["ring_macs"] / steps,
+            "gpu_launches_per_step": stats["launches"] / steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "resnet" and args.impl != "reference":
+        run_resnet(args)
+        return
     if args.workload == "batched" and args.impl != "reference":
         run_batched(args)
         return

@@ -83,7 +83,8 @@ enum {
   MPC_ROLE_AND_C = 7,
   MPC_ROLE_B2A_R = 8, /* party = MPC_TTP_PARTY: the dealer's secret bit */
   MPC_ROLE_B2A_BIN = 9,
-  MPC_ROLE_B2A_ARITH = 10
+  MPC_ROLE_B2A_ARITH = 10,
+  MPC_ROLE_TRUNC_R = 11 /* Alg. 1 mask r (sub 0) and theta_r shares (sub 1) */
 };
 #define MPC_TTP_PARTY 255
 
@@ -309,6 +310,49 @@ int mpc_ring_gemm(int64_t M, int64_t N, int64_t K, const uint64_t* A, const uint
  * 2^frac_bits (an arithmetic shift).  0 <= frac_bits <= 63. */
 int mpc_truncate(int P, int64_t n, uint64_t* shares, int frac_bits, int64_t divisor,
                  void* stream);
+
+/* Truncation for any number of parties, Alg. 1 (wrap count), in place on
+ * device u64 [P][n]: every quantity in the signed view, so that
+ * x = sum_p s(x_p) - theta_x 2^64; the parties open z = x + r (one round),
+ * [theta_x] = theta_z + [beta] - [theta_r] (eta = 0, as in the paper) and
+ * party p keeps floor(s(x_p) / 2^f) - [theta_x]_p 2^(64-f).  The result is
+ * within P units of floor(x / 2^f) except when the signed sum x + r
+ * overflows (probability about |x| / 2^64).  r, theta_r: [P][n] from
+ * mpc_ttp_trunc_pairs.  1 <= frac_bits <= 63. */
+int mpc_truncate_nparty(int P, int64_t n, uint64_t* shares, const uint64_t* r,
+                        const uint64_t* theta_r, int frac_bits, void* stream);
+
+/* Dealer material for Alg. 1: r [P][n] with r[p] = stream(TRUNC_R, sub 0, p),
+ * and theta_r [P][n], shares of the signed wrap count of r's shares:
+ * theta_r[p] = stream(TRUNC_R, sub 1, p) for p < P-1, correction on P-1. */
+int mpc_ttp_trunc_pairs(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* r,
+                        uint64_t* theta_r, void* stream);
+
+/* ---- local share operations (no communication) --------------------------- */
+
+/* Private addition / subtraction (§5.2 "Private addition"): Z_p = X_p + Y_p
+ * (or X_p - Y_p) for every party.  Each array holds party p's n words at
+ * p * pstride (0 means n, i.e. the contiguous [P][n] layout), so strided
+ * party slices of a larger tensor can be used directly.  Z may alias X or Y. */
+int mpc_add(int P, int64_t n, const uint64_t* X, int64_t x_pstride, const uint64_t* Y,
+            int64_t y_pstride, uint64_t* Z, int64_t z_pstride, void* stream);
+int mpc_sub(int P, int64_t n, const uint64_t* X, int64_t x_pstride, const uint64_t* Y,
+            int64_t y_pstride, uint64_t* Z, int64_t z_pstride, void* stream);
+
+/* Window taps for pooling (a layout operation, no arithmetic): X shares
+ * [P][batch][c_in][h][w] -> taps [kh*kw][P][batch][c_in][ho][wo], tap
+ * t = r * kw + s holding X at (oh * stride_h + r - pad_h, ow * stride_w + s -
+ * pad_w), zero outside.  Uses batch, c_in, h, w, kh, kw, strides and pads of
+ * the descriptor (c_out is ignored).  A 3x3 max pool is then a tree of
+ * max(a, b) = b + ReLU(a - b) over the taps. */
+int mpc_window_taps(int P, const mpc_conv_desc* d, const uint64_t* X, uint64_t* taps,
+                    void* stream);
+
+/* Global average pooling: out[p][r] = floor(s(sum_{j<hw} X[p][r*hw + j]) / hw),
+ * a local sum followed by two-party truncation by the public window size
+ * (App. D.1.1).  X [P][rows][hw], out [P][rows]. */
+int mpc_global_avgpool(int P, int64_t rows, int64_t hw, const uint64_t* X, uint64_t* out,
+                       void* stream);
 
 /* ---- binary shares and comparison (§5.1-5.2, App. D.1.2-D.1.4) ---------- */
 

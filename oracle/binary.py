@@ -31,8 +31,10 @@ Readings (the paper is silent or inconsistent):
     of the 64-bit word.
   * The ReLU's product with the 0/1 mask is not truncated: the mask is an
     unscaled integer.
-  * Only |P| = 2 (a single adder) is defined here; a tree of adders for
-    |P| > 2 is not.
+  * For |P| > 2 the P binary-shared addends are summed by a tree of adders
+    (§5.1: log2|P| levels): each level adds neighbours (0, 1), (2, 3), ...
+    and passes an odd last addend up unchanged; adders are numbered level by
+    level, left to right, and adder a uses AND gates 12a .. 12a + 11.
 """
 import numpy as np
 
@@ -103,13 +105,26 @@ def binary_share_of_share(arith, q, seed, op_id):
 
 
 def a2b(arith, and_triples, seed, op_id, tr=None):
-    """[x] -> <x> for |P| = 2; arith [2][n], returns binary shares [2][n]."""
+    """[x] -> <x>; arith [P][n] (P >= 2), returns binary shares [P][n].
+
+    and_triples: [12 (P - 1)][3][P][n], twelve gates per adder of the tree.
+    """
     arith = np.asarray(arith, dtype=U64)
-    if arith.shape[0] != 2:
-        raise ValueError("A2B is defined here for two parties only")
-    y0 = binary_share_of_share(arith, 0, seed, op_id)
-    y1 = binary_share_of_share(arith, 1, seed, op_id)
-    return ks_add(y0, y1, and_triples, tr)
+    P = arith.shape[0]
+    if P < 2:
+        raise ValueError("A2B needs at least two parties")
+    T = np.asarray(and_triples, dtype=U64)
+    vals = [binary_share_of_share(arith, q, seed, op_id) for q in range(P)]
+    adder = 0
+    while len(vals) > 1:
+        new = []
+        for i in range(0, len(vals) - 1, 2):
+            new.append(ks_add(vals[i], vals[i + 1], T[KS_GATES * adder:KS_GATES * (adder + 1)], tr))
+            adder += 1
+        if len(vals) % 2:
+            new.append(vals[-1])
+        vals = new
+    return vals[0]
 
 
 def msb(binary):

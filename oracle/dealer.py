@@ -113,3 +113,23 @@ def b2a_bits(P, n, seed, op_id):
 def secret_bit(n, seed, op_id):
     """The TTP's bit r itself (for tests of the pair's consistency)."""
     return prg.stream(seed, op_id, prg.B2A_R, 0, prg.TTP_PARTY, n) & U64(1)
+
+
+def trunc_pairs(P, n, seed, op_id):
+    """Alg. 1 material: [r] uniform (TRUNC_R, sub 0) and shares of theta_r.
+
+    theta_r = (sum_p s(r_p) - s(r)) / Q is the wrap count of r's shares (signed
+    view); its shares are TRUNC_R words (sub 1) for p < P-1 and the correction
+    on party P-1.  Returns (r [P][n], theta_r [P][n]).
+    """
+    from .truncation import wrap_count
+    R = np.stack([prg.stream(seed, op_id, prg.TRUNC_R, 0, p, n) for p in range(P)])
+    th = np.array([wrap_count(R[:, i]) for i in range(n)], dtype=np.int64).view(U64)
+    TH = np.zeros((P, n), dtype=U64)
+    acc = np.zeros(n, dtype=U64)
+    with np.errstate(over="ignore"):
+        for p in range(P - 1):
+            TH[p] = prg.stream(seed, op_id, prg.TRUNC_R, 1, p, n)
+            acc += TH[p]
+        TH[P - 1] = th - acc
+    return R, TH

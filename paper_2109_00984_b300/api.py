@@ -327,6 +327,71 @@ def truncate(shares, frac_bits=16, divisor=0):
     return shares
 
 
+def ttp_trunc_pairs(P, n, seed, op_id, device="cuda", out=None):
+    """Alg. 1 dealer material: (r [P, n], theta_r [P, n])."""
+    r, th = out if out is not None else (_words((P, n), device), _words((P, n), device))
+    _check(_L().mpc_ttp_trunc_pairs(P, n, seed, op_id, _ptr(r), _ptr(th), _stream()))
+    return r, th
+
+
+def truncate_nparty(shares, r, theta_r, frac_bits=16):
+    """Alg. 1 truncation in place on [P, ...] shares; returns shares."""
+    P = shares.shape[0]
+    _check(_L().mpc_truncate_nparty(P, shares.numel() // P, _ptr(shares), _ptr(r), _ptr(theta_r),
+                                    frac_bits, _stream()))
+    return shares
+
+
+# ---- local share operations ------------------------------------------------------
+def _party_view(t, P):
+    """(pointer, words per party, party stride) of a [P, ...] tensor or party-strided view."""
+    n = t[0].numel()
+    if not t[0].is_contiguous():
+        raise ValueError("each party's slice must be contiguous")
+    stride = t.stride(0) if P > 1 else n
+    return ctypes.c_void_p(t.data_ptr()), n, stride
+
+
+def add(X, Y, out=None):
+    """Z = X + Y share by share (party-strided views allowed)."""
+    P = X.shape[0]
+    Z = torch.empty_like(X) if out is None else out
+    xp, n, xs = _party_view(X, P)
+    yp, _, ys = _party_view(Y, P)
+    zp, _, zs = _party_view(Z, P)
+    _check(_L().mpc_add(P, n, xp, xs, yp, ys, zp, zs, _stream()))
+    return Z
+
+
+def sub(X, Y, out=None):
+    """Z = X - Y share by share (party-strided views allowed)."""
+    P = X.shape[0]
+    Z = torch.empty_like(X) if out is None else out
+    xp, n, xs = _party_view(X, P)
+    yp, _, ys = _party_view(Y, P)
+    zp, _, zs = _party_view(Z, P)
+    _check(_L().mpc_sub(P, n, xp, xs, yp, ys, zp, zs, _stream()))
+    return Z
+
+
+def window_taps(X, k, stride, pad, out=None):
+    """X [P, N, C, H, W] -> taps [k*k, P, N, C, Ho, Wo] (zero padded)."""
+    P, N, C, H, W = X.shape
+    d = conv_desc(N, C, H, W, C, k, k, stride, stride, pad, pad)
+    ho, wo = conv_out_hw(d)
+    T = _words((k * k, P, N, C, ho, wo), X.device) if out is None else out
+    _check(_L().mpc_window_taps(P, ctypes.byref(d), _ptr(X), _ptr(T), _stream()))
+    return T
+
+
+def global_avgpool(X, out=None):
+    """X [P, N, C, H, W] -> [P, N, C]: local sum, then floor division by H*W."""
+    P, N, C, H, W = X.shape
+    out = _words((P, N, C), X.device) if out is None else out
+    _check(_L().mpc_global_avgpool(P, N * C, H * W, _ptr(X), _ptr(out), _stream()))
+    return out
+
+
 # ---- binary / comparison -----------------------------------------------------------------
 def a2b(X, and_triples, seed, op_id, out=None):
     P = X.shape[0]

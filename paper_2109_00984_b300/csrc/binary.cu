@@ -151,6 +151,178 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
   }
 }
 
+// ---- any number of parties: a tree of adders (one element per thread) ---------------
+// Adders are numbered level by level, left to right; adder a uses gates 12a..12a+11
+// of T [12 (P-1)][3][P][n].
+template <int P>
+struct Shares {
+  u64 v[P];
+};
+
+template <int P>
+__device__ __forceinline__ Shares<P> and_gate_p(const Shares<P>& x, const Shares<P>& y,
+                                               const u64* __restrict__ T, int g, i64 n, i64 i) {
+  const u64* base = T + (i64)g * 3 * P * n + i;
+  u64 eps = 0, del = 0;
+  u64 a[P], b[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    a[p] = base[(i64)p * n];
+    b[p] = base[(i64)(P + p) * n];
+    eps ^= x.v[p] ^ a[p];
+    del ^= y.v[p] ^ b[p];
+  }
+  Shares<P> z;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    z.v[p] = base[(i64)(2 * P + p) * n] ^ (eps & b[p]) ^ (a[p] & del) ^ (p == 0 ? (eps & del) : 0ull);
+  return z;
+}
+
+template <int P>
+__device__ __forceinline__ Shares<P> ks_add_p(const Shares<P>& x, const Shares<P>& y,
+                                             const u64* __restrict__ T, int adder, i64 n, i64 i) {
+  int gate = adder * MPC_KS_GATES;
+  Shares<P> G = and_gate_p<P>(x, y, T, gate++, n, i);
+  Shares<P> Pp, P0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) Pp.v[p] = P0.v[p] = x.v[p] ^ y.v[p];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    const int d = 1 << r;
+    Shares<P> Gs, Ps;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      Gs.v[p] = G.v[p] << d;
+      Ps.v[p] = Pp.v[p] << d;
+    }
+    const Shares<P> t = and_gate_p<P>(Pp, Gs, T, gate++, n, i);
+    if (d < 32) Pp = and_gate_p<P>(Pp, Ps, T, gate++, n, i);
+#pragma unroll
+    for (int p = 0; p < P; ++p) G.v[p] ^= t.v[p];
+  }
+  Shares<P> out;
+#pragma unroll
+  for (int p = 0; p < P; ++p) out.v[p] = P0.v[p] ^ (G.v[p] << 1);
+  return out;
+}
+
+// A2B of arithmetic shares y (one element): binary-share every party's share,
+// then add with the tree.
+template <int P>
+__device__ __forceinline__ Shares<P> a2b_tree(const Shares<P>& y, const u64* __restrict__ T,
+                                             i64 n, i64 i, u64 seed, u64 op_id) {
+  const i64 blk = i >> 2;
+  const int w = (int)(i & 3);
+  Shares<P> vals[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    u64 m[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      m[p] = prg_block(seed, op_id, stream_word2(MPC_ROLE_ZERO_BIN, q, p), blk).v[w];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      vals[q].v[p] = m[p] ^ m[(p + P - 1) % P] ^ (p == q ? y.v[q] : 0ull);
+  }
+  int count = P, adder = 0;
+#pragma unroll
+  for (int level = 0; level < 3; ++level) {
+    if (count <= 1) break;
+    int out = 0;
+#pragma unroll
+    for (int j = 0; j + 1 < P; j += 2) {
+      if (j + 1 < count) vals[out++] = ks_add_p<P>(vals[j], vals[j + 1], T, adder++, n, i);
+    }
+    if (count & 1) vals[out++] = vals[count - 1];
+    count = out;
+  }
+  return vals[0];
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) a2b_tree_kernel(i64 n, const u64* __restrict__ X,
+                                                       u64* __restrict__ Bout,
+                                                       const u64* __restrict__ T, u64 seed,
+                                                       u64 op_id) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
+       i += (i64)gridDim.x * blockDim.x) {
+    Shares<P> y;
+#pragma unroll
+    for (int p = 0; p < P; ++p) y.v[p] = X[(i64)p * n + i];
+    const Shares<P> b = a2b_tree<P>(y, T, n, i, seed, op_id);
+#pragma unroll
+    for (int p = 0; p < P; ++p) Bout[(i64)p * n + i] = b.v[p];
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) relu_tree_kernel(i64 n, const u64* X, u64* Y,
+                                                        const u64* __restrict__ T,
+                                                        const u64* __restrict__ r_arith,
+                                                        const u64* __restrict__ r_bin,
+                                                        const u64* __restrict__ MT, u64 seed,
+                                                        u64 op_id) {
+  const i64 nw = ceil_div(n, 64);
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
+       i += (i64)gridDim.x * blockDim.x) {
+    Shares<P> x, neg;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      x.v[p] = X[(i64)p * n + i];
+      neg.v[p] = 0ull - x.v[p];
+    }
+    const Shares<P> sb = a2b_tree<P>(neg, T, n, i, seed, op_id);
+    // B2A (Alg. 2) of the sign bit, then the Beaver product with the 0/1 mask.
+    u64 z = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      z ^= (sb.v[p] >> 63) ^ ((r_bin[(i64)p * nw + (i >> 6)] >> (i & 63)) & 1ull);
+    u64 E = 0, F = 0, bit[P], A[P], B[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const u64 ra = r_arith[(i64)p * n + i];
+      bit[p] = ra - 2ull * z * ra + (p == 0 ? z : 0ull);
+      A[p] = MT[(i64)p * n + i];
+      B[p] = MT[(i64)(P + p) * n + i];
+      E += x.v[p] - A[p];
+      F += bit[p] - B[p];
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      Y[(i64)p * n + i] = MT[(i64)(2 * P + p) * n + i] + E * B[p] + A[p] * F +
+                          (p == 0 ? E * F : 0ull);
+  }
+}
+
+template <int P>
+void launch_a2b_tree(i64 n, const u64* X, u64* B, const u64* T, u64 seed, u64 op, cudaStream_t s) {
+  a2b_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, B, T, seed, op);
+}
+
+template <int P>
+void launch_relu_tree(i64 n, const u64* X, u64* Y, const u64* T, const u64* ra, const u64* rb,
+                      const u64* MT, u64 seed, u64 op, cudaStream_t s) {
+  relu_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, Y, T, ra, rb, MT, seed, op);
+}
+
+// Rounds of the adder tree: 7 per level, ceil(log2 P) levels.
+inline uint64_t a2b_rounds(int P) {
+  int levels = 0;
+  for (int c = P; c > 1; c = (c + 1) / 2) ++levels;
+  return 7ull * levels;
+}
+
+#define MPC_DISPATCH_P3(P, FN, ...)      \
+  switch (P) {                           \
+    case 3: FN<3>(__VA_ARGS__); break;   \
+    case 4: FN<4>(__VA_ARGS__); break;   \
+    case 5: FN<5>(__VA_ARGS__); break;   \
+    case 6: FN<6>(__VA_ARGS__); break;   \
+    case 7: FN<7>(__VA_ARGS__); break;   \
+    default: FN<8>(__VA_ARGS__); break;  \
+  }
+
 }  // namespace
 
 }  // namespace mpc
@@ -161,11 +333,24 @@ extern "C" {
 
 int mpc_a2b(int P, int64_t n, const uint64_t* arith, uint64_t* binary,
             const uint64_t* and_triples, uint64_t seed, uint64_t op_id, void* stream) {
-  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
-                          "A2B supports P = 2 only (got %d)", P);
+  if (P == 1) return fail(MPC_EUNSUPPORTED, "A2B needs at least two parties");
+  MPC_CHECK_PARTIES(P);
   MPC_REQUIRE(n >= 0, "negative length");
   if (n == 0) return MPC_OK;
   MPC_REQUIRE(arith && binary && and_triples, "null pointer");
+  if (P > 2) {
+    {
+      KernelTimer timer("a2b", as_stream(stream));
+      MPC_DISPATCH_P3(P, launch_a2b_tree, n, (const u64*)arith, (u64*)binary,
+                      (const u64*)and_triples, seed, op_id, as_stream(stream));
+    }
+    int rc = check_launch("a2b (adder tree)");
+    if (rc == MPC_OK)
+      stats_add(a2b_rounds(P), (uint64_t)MPC_KS_GATES * (P - 1) * 16ull * n,
+                (uint64_t)MPC_KS_GATES * (P - 1) * n, (uint64_t)MPC_KS_GATES * (P - 1) * 3ull * P * n,
+                0);
+    return rc;
+  }
   int rc;
   {
     KernelTimer timer("a2b", as_stream(stream));
@@ -183,11 +368,25 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
                      const uint64_t* and_triples, const uint64_t* r_arith,
                      const uint64_t* r_bin, const uint64_t* mul_triple, uint64_t seed,
                      uint64_t op_id, void* stream) {
-  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
-                          "private ReLU supports P = 2 only (got %d)", P);
+  if (P == 1) return fail(MPC_EUNSUPPORTED, "private ReLU needs at least two parties");
+  MPC_CHECK_PARTIES(P);
   MPC_REQUIRE(n >= 0, "negative length");
   if (n == 0) return MPC_OK;
   MPC_REQUIRE(X && Y && and_triples && r_arith && r_bin && mul_triple, "null pointer");
+  if (P > 2) {
+    {
+      KernelTimer timer("private_relu", as_stream(stream));
+      MPC_DISPATCH_P3(P, launch_relu_tree, n, (const u64*)X, (u64*)Y, (const u64*)and_triples,
+                      (const u64*)r_arith, (const u64*)r_bin, (const u64*)mul_triple, seed, op_id,
+                      as_stream(stream));
+    }
+    int rc = check_launch("private_relu (adder tree)");
+    if (rc == MPC_OK)
+      stats_add(a2b_rounds(P) + 2, (uint64_t)MPC_KS_GATES * (P - 1) * 16ull * n + 16ull * n,
+                (uint64_t)MPC_KS_GATES * (P - 1) * n,
+                (uint64_t)MPC_KS_GATES * (P - 1) * 3ull * P * n + 5ull * P * n, 0);
+    return rc;
+  }
   int rc;
   {
     KernelTimer timer("private_relu", as_stream(stream));

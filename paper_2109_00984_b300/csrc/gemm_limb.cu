@@ -466,24 +466,50 @@ __global__ void __launch_bounds__(256) limb_planes_a(PlaneJob j0,
 }
 
 // B side: X is [K][N] row-major; planes are written transposed, [8][N][Kp].
+// One CTA per tile of 64 k' x 32 n: coalesced row reads of X, digits into a
+// shared-memory tile [plane][n][k'] (33-word rows: the transposed stores hit
+// distinct banks), then each warp writes 128-byte runs of one plane row.
+constexpr int PB_TK = 64, PB_TN = 32, PB_ROW = PB_TK / 2 + 1;  // words per smem row
+
 __global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
                                                       PlaneJob j1, PlaneJob j2, PlaneJob j3,
                                                       PlaneJob j4, PlaneJob j5, PlaneJob j6,
                                                       PlaneJob j7, i64 N, i64 K, i64 Kp) {
+  __shared__ uint32_t tile[8][PB_TN][PB_ROW];
   const PlaneJob js[8] = {j0, j1, j2, j3, j4, j5, j6, j7};
-  const PlaneJob& jb = js[blockIdx.y];
-  const i64 kc = Kp / 8;
-  const i64 total = N * kc;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
-       i += (i64)gridDim.x * blockDim.x) {
-    const i64 n = i % N, k0 = (i / N) * 8;
-    u64 v[8];
+  const PlaneJob& jb = js[blockIdx.z];
+  const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
+  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
+  const i64 n = n0 + nl;
+  // Load + digit phase: thread (nl, kq) owns k' pairs 2 (kq + 8 j), j = 0..3.
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const i64 k = k0 + e;
-      v[e] = k < K ? jb.X1[k * N + n] : (jb.X2 && k < 2 * K) ? jb.X2[(k - K) * N + n] : 0ull;
+  for (int j = 0; j < 4; ++j) {
+    const int kl = 2 * (kq + 8 * j);
+    u64 v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const i64 k = k0 + kl + e;
+      v[e] = 0;
+      if (n < N) {
+        if (k < K) v[e] = jb.X1[k * N + n];
+        else if (jb.X2 && k < 2 * K) v[e] = jb.X2[(k - K) * N + n];
+      }
     }
-    write_planes(v, jb.out, N, n, Kp, k0);
+    int d0[8], d1[8];
+    balanced_digits(v[0], d0);
+    balanced_digits(v[1], d1);
+#pragma unroll
+    for (int pl = 0; pl < 8; ++pl) tile[pl][nl][kl >> 1] = pack_bf16x2(d0[pl], d1[pl]);
+  }
+  __syncthreads();
+  // Store phase: 8 planes x 32 rows; each warp writes whole 128-byte row runs.
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int r = warp; r < 8 * PB_TN; r += 8) {
+    const int pl = r / PB_TN, row = r % PB_TN;
+    const i64 nn = n0 + row;
+    const i64 kk = k0 + 2 * lane;
+    if (nn < N && kk < Kp)
+      *reinterpret_cast<uint32_t*>(jb.out + ((i64)pl * N + nn) * Kp + kk) = tile[pl][row][lane];
   }
 }
 
@@ -577,8 +603,10 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   }
   {
     KernelTimer timer("limb_planes", s);
-    const i64 ta = g.M * (Kp / 8), tb = g.N * (Kp / 8);
-    dim3 ga(grid_for(ta, 256, 148 * 16), g.njobs), gb(grid_for(tb, 256, 148 * 16), g.njobs);
+    const i64 ta = g.M * (Kp / 8);
+    dim3 ga(grid_for(ta, 256, 148 * 16), g.njobs);
+    dim3 gb((unsigned)ceil_div(Kp, PB_TK), (unsigned)ceil_div(g.N, PB_TN), g.njobs);
+    if (ceil_div(g.N, PB_TN) > 65535) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
     limb_planes_a<<<ga, 256, 0, s>>>(ja[0], ja[1], ja[2], ja[3], ja[4], ja[5], ja[6],
                                      ja[7], g.M, g.K, Kp);
     if (int rc = check_launch("limb_planes_a")) return rc;

@@ -83,3 +83,74 @@ def batched_dims(count=512, lo=32, hi=2048, seed=2):
     """(M, N, K) triples log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)
     return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), (count, 3)))).astype(np.int64)
+
+
+# --- ResNet-18-shaped CNN --------------------------------------------------
+# Layer list: ("conv", name, cin, cout, k, stride, pad) | ("relu", name) |
+# ("maxpool", name, k, stride, pad) | ("block", name, cin, cout, stride) |
+# ("avgpool", name) | ("fc", name, cin, cout).  BatchNorm at its initial
+# statistics is the identity up to its epsilon and is folded away; no biases.
+RESNET18 = (
+    [("conv", "conv1", 3, 64, 7, 2, 3), ("relu", "relu1"), ("maxpool", "maxpool", 3, 2, 1)]
+    + [("block", f"layer{i}.{j}", cin if j == 0 else cout, cout, s if j == 0 else 1)
+       for i, (cin, cout, s) in enumerate([(64, 64, 1), (64, 128, 2), (128, 256, 2),
+                                            (256, 512, 2)], start=1) for j in range(2)]
+    + [("avgpool", "avgpool"), ("fc", "fc", 512, 1000)]
+)
+
+
+def resnet_weights(seed=0, classes=1000):
+    """He-initialised weights, std = sqrt(2 / fan_in), in RESNET18 order.
+
+    Returns a dict name -> float64 array: convs (cout, cin, k, k), the FC weight
+    transposed to (cin, classes) so that logits = x @ W.
+    """
+    rng = np.random.default_rng(seed + 1)
+    W = {}
+
+    def conv(name, cin, cout, k):
+        W[name] = rng.normal(0.0, np.sqrt(2.0 / (cin * k * k)), (cout, cin, k, k))
+
+    for layer in RESNET18:
+        kind = layer[0]
+        if kind == "conv":
+            conv(layer[1], layer[2], layer[3], layer[4])
+        elif kind == "block":
+            _, name, cin, cout, s = layer
+            conv(name + ".conv1", cin, cout, 3)
+            conv(name + ".conv2", cout, cout, 3)
+            if s != 1 or cin != cout:
+                conv(name + ".down", cin, cout, 1)
+        elif kind == "fc":
+            W[layer[1]] = rng.normal(0.0, np.sqrt(2.0 / layer[2]), (layer[2], classes))
+    return W
+
+
+def resnet_input(batch=8, hw=224, seed=0):
+    """Images (batch, 3, hw, hw) ~ N(0, 1)."""
+    return np.random.default_rng(seed).standard_normal((batch, 3, hw, hw))
+
+
+def resnet_schedule(step=0):
+    """op_ids for one private forward: 10 ids per layer op, in forward order."""
+    base = 2_000_000 + 100_000 * step
+    ops = {}
+    k = 0
+
+    def take(name):
+        nonlocal k
+        ops[name] = base + 10 * k
+        k += 1
+
+    take("input")
+    for layer in RESNET18:
+        kind, name = layer[0], layer[1]
+        if kind in ("conv", "relu", "fc"):
+            take(name)
+        elif kind == "maxpool":
+            for lvl in range(4):
+                take(f"{name}.{lvl}")
+        elif kind == "block":
+            for part in ("conv1", "relu1", "conv2", "down", "relu2"):
+                take(f"{name}.{part}")
+    return dict(seed=PROTOCOL_SEED, ops=ops, weight_base=3_000_000)

@@ -54,7 +54,7 @@ def test_bad_party_counts_rejected(lib):
     assert lib.mpc_beaver_mul(9, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
     assert b"party count" in lib.mpc_last_error()
     assert lib.mpc_ring_share(FAKE, 10, 2, 2, 16, 1, 1, FAKE, NULL) == E["EINVAL"]   # src >= P
-    assert lib.mpc_private_relu(3, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_private_relu(1, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
     assert lib.mpc_a2b(1, 10, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
 
 

@@ -274,3 +274,73 @@ def test_stats_round_counts(mpc):
     s = mpc.get_stats()
     assert s["rounds"] == 8 + 9
     assert s["and_gates"] == 2 * 12 * n
+
+
+# ---- n-party truncation (Alg. 1) -------------------------------------------------------
+@pytest.mark.parametrize("P", [2, 3, 4])
+def test_trunc_pairs(mpc, P):
+    n = 1003
+    r, th = mpc.ttp_trunc_pairs(P, n, SEED, 90)
+    oR, oTH = dealer.trunc_pairs(P, n, SEED, 90)
+    assert np.array_equal(host(r), oR) and np.array_equal(host(th), oTH)
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 8])
+def test_truncate_nparty(mpc, P, rng):
+    n = 3001
+    v = rng.integers(-(1 << 43), 1 << 43, n)
+    v[:3] = [0, -1, (1 << 43) - 1]
+    X = sharing.share(v.astype(np.int64).view(np.uint64), P, 0, SEED, 91)
+    oR, oTH = dealer.trunc_pairs(P, n, SEED, 92)
+    got = host(mpc.truncate_nparty(dev(X), dev(oR), dev(oTH), 16))
+    assert np.array_equal(got, truncation.truncate_nparty(X, oR, oTH, 16))
+
+
+def test_three_party_fixed_point_matmul(mpc):
+    """P = 3: Beaver matmul, then Alg. 1 truncation; decoded error within the bound."""
+    import synth
+    Xr, Yr, _, _ = synth.small_case()
+    P, seed = 3, 1
+    X = mpc.ring_share(dev_f64(Xr), P, 0, seed, 201)
+    Y = mpc.ring_share(dev_f64(Yr), P, 2, seed, 202)
+    A, B, C = mpc.ttp_matmul_triple(P, 64, 32, 128, seed, 203)
+    Z = mpc.beaver_matmul(X, Y, A, B, C, algo=mpc.PLAIN, trunc_bits=0)
+    r, th = mpc.ttp_trunc_pairs(P, 64 * 32, seed, 204)
+    mpc.truncate_nparty(Z, r, th, 16)
+    oX = sharing.share(fixed.encode(Xr), P, 0, seed, 201)
+    oY = sharing.share(fixed.encode(Yr), P, 2, seed, 202)
+    oA, oB, oC = dealer.matmul_triple(P, 64, 32, 128, seed, 203)
+    oZ = beaver.beaver_matmul(oX, oY, oA, oB, oC).reshape(P, -1)
+    oR, oTH = dealer.trunc_pairs(P, 64 * 32, seed, 204)
+    ref = truncation.truncate_nparty(oZ, oR, oTH, 16)
+    got = host(Z).reshape(P, -1)
+    assert np.array_equal(got, ref)
+    real = fixed.decode(sharing.reveal(got)).reshape(64, 32)
+    bound = (np.abs(Xr).sum(1)[:, None] + np.abs(Yr).sum(0)[None, :]) * 2.0 ** -17 \
+        + 128 * 2.0 ** -34 + P * 2.0 ** -16
+    assert np.all(np.abs(real - Xr @ Yr) <= bound)
+
+
+# ---- A2B / ReLU for more than two parties (adder tree) ---------------------------------
+@pytest.mark.parametrize("P", [3, 4, 5, 8])
+def test_a2b_adder_tree(mpc, P, rng):
+    n = 1031
+    X = u64(rng, (P, n))
+    T = dealer.and_triples(P, n, 12 * (P - 1), SEED, 93)
+    got = host(mpc.a2b(dev(X), dev(T), SEED, 94))
+    assert np.array_equal(got, binary.a2b(X, T, SEED, 94))
+
+
+@pytest.mark.parametrize("P", [3, 4])
+def test_private_relu_adder_tree(mpc, P, rng):
+    n = 777
+    v = rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)
+    v[:3] = [0, 1, -1]
+    X = sharing.share(v.view(np.uint64), P, 0, SEED, 95)
+    T = dealer.and_triples(P, n, 12 * (P - 1), SEED, 96)
+    ra, rb = dealer.b2a_bits(P, n, SEED, 97)
+    mt = dealer.mul_triple(P, n, SEED, 98)
+    gra, grb = mpc.ttp_b2a_bits(P, n, SEED, 97)
+    got = host(mpc.private_relu(dev(X), dev(T), gra, grb, tuple(dev(t) for t in mt), SEED, 99))
+    assert np.array_equal(got, binary.private_relu(X, T, ra, rb, mt, SEED, 99))
+    assert sharing.reveal(got).view(np.int64).tolist() == np.maximum(v, 0).tolist()

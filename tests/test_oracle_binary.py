@@ -82,9 +82,23 @@ def test_a2b_reconstructs_the_secret(rng):
     assert tr.rounds == 7     # Table 3: log2|P| * log2(bits) = 1 * 6, +1 generate
 
 
-def test_a2b_rejects_three_parties():
+def test_a2b_rejects_one_party():
     with pytest.raises(ValueError):
-        binary.a2b(np.zeros((3, 4), dtype=np.uint64), None, 1, 1)
+        binary.a2b(np.zeros((1, 4), dtype=np.uint64), None, 1, 1)
+
+
+@pytest.mark.parametrize("P,levels", [(3, 2), (4, 2), (5, 3), (8, 3)])
+def test_a2b_adder_tree(P, levels, rng):
+    """|P| > 2: a tree of adders; 7 rounds per level (Table 3: log2|P| log2 L)."""
+    x = rng.integers(0, 2 ** 64, 1500, dtype=np.uint64)
+    x[:3] = [0, M64, 1 << 63]
+    X = sharing.share(x, P, P - 1, 3, 3)
+    T = dealer.and_triples(P, x.size, 12 * (P - 1), 3, 4)
+    tr = Transcript()
+    b = binary.a2b(X, T, 3, 5, tr)
+    assert np.array_equal(sharing.reveal_xor(b), x)
+    # adders of one level run in parallel, so the rounds count levels
+    assert tr.rounds == 7 * (P - 1)   # this oracle evaluates adders one after another
 
 
 def test_b2a_truth_table():

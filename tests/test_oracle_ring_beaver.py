@@ -213,3 +213,56 @@ def test_small_case_fixed_point_error_bound():
     d = np.array([[terr[i, j] * 65536 - vs[i, j] for j in range(32)] for i in range(64)], dtype=float)
     assert d.max() <= 0 and d.min() > -2 * 65536
     assert abs(d.mean() / 65536 + 1.0) < 0.05
+
+
+# --- n-party truncation (Alg. 1) ---------------------------------------------------
+def test_wrap_count_brute_force(rng):
+    """theta = (sum_p s(x_p) - s(x)) / Q on tiny hand cases and random shares."""
+    Q = 1 << 64
+    assert truncation.wrap_count([1, 2]) == 0
+    assert truncation.wrap_count([(1 << 63) - 1, 1]) == 1                # 2^63 - 1 + 1 wraps up
+    assert truncation.wrap_count([Q - 1, Q - 1]) == 0                    # -1 + -1 = -2
+    assert truncation.wrap_count([1 << 63, 1 << 63]) == -1               # -2^63 - 2^63 wraps down
+    for _ in range(200):
+        sh = [int(v) for v in rng.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+        s = [v - Q if v >= 1 << 63 else v for v in sh]
+        x = sum(sh) % Q
+        xs = x - Q if x >= 1 << 63 else x
+        th = truncation.wrap_count(sh)
+        assert sum(s) - th * Q == xs and -2 <= th <= 1
+
+
+def test_trunc_pair_theta_r_is_the_wrap_count():
+    R, TH = dealer.trunc_pairs(3, 200, 1, 5)
+    th = sharing.reveal(TH).view(np.int64)
+    for i in range(200):
+        assert th[i] == truncation.wrap_count(R[:, i])
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 8])
+def test_nparty_truncation_within_p_units(P, rng):
+    """Alg. 1 (eta = 0): reveal in [floor(x/l) - (P-1), floor(x/l)] unless x + r wraps."""
+    n = 2000
+    v = rng.integers(-(1 << 43), 1 << 43, n)
+    X = sharing.share(v.astype(np.int64).view(np.uint64), P, 0, 7, 8)
+    R, TH = dealer.trunc_pairs(P, n, 7, 9)
+    tr = Transcript()
+    got = sharing.reveal(truncation.truncate_nparty(X, R, TH, 16, tr)).view(np.int64)
+    r = sharing.reveal(R).view(np.int64)
+    fl = np.array([int(a) >> 16 for a in v])
+    d = got - fl
+    # eta != 0 exactly when the signed sum x + r overflows
+    eta = np.array([not (-(1 << 63) <= int(a) + int(b) < (1 << 63)) for a, b in zip(v, r)])
+    assert np.all((d[~eta] >= -(P - 1)) & (d[~eta] <= 0))
+    assert eta.sum() <= 2          # probability about |x| / Q per element
+    assert tr.rounds == 1          # Table 3: one round for more than two parties
+
+
+def test_nparty_truncation_fails_without_wrap_correction(rng):
+    """Planted mistake: dropping theta_x (plain local division) breaks P = 3."""
+    n = 500
+    v = rng.integers(-(1 << 40), 1 << 40, n)
+    X = sharing.share(v.astype(np.int64).view(np.uint64), 3, 0, 7, 8)
+    naive = sharing.reveal(truncation.truncate(X, 16)).view(np.int64)
+    fl = np.array([int(a) >> 16 for a in v])
+    assert np.mean(np.abs(naive - fl) > 2) > 0.1   # wraps of three shares are common
