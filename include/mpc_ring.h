@@ -376,6 +376,18 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
                      const uint64_t* r_bin, const uint64_t* mul_triple, uint64_t seed,
                      uint64_t op_id, void* stream);
 
+/* Private ReLU with the dealer fused in (P = 2): the same result as
+ *   mpc_ttp_and_triples(2, n, 12, seed, op_id) -> T,
+ *   mpc_ttp_b2a_bits(2, n, seed, op_id + 1) -> r_arith, r_bin,
+ *   mpc_ttp_mul_triple(2, n, seed, op_id + 2) -> A, B, C,
+ *   mpc_private_relu(2, n, X, Y, T, r_arith, r_bin, [A B C], seed, op_id + 3),
+ * bit for bit, but every piece of dealer material is regenerated in registers
+ * from its Philox stream instead of being written to and read from memory
+ * (the trusted dealer and both parties are simulated in one kernel).  X, Y
+ * device u64 [2][n] (may alias).  Uses op ids op_id .. op_id + 3. */
+int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
+                           uint64_t op_id, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

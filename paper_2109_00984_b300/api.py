@@ -413,3 +413,12 @@ def private_relu(X, and_triples, r_arith, r_bin, mul_triple, seed, op_id, out=No
     _check(_L().mpc_private_relu(P, n, _ptr(X), _ptr(out), _ptr(and_triples), _ptr(r_arith),
                                  _ptr(r_bin), _ptr(mt), seed, op_id, _stream()))
     return out
+
+
+def private_relu_fused(X, seed, op_id, out=None):
+    """ReLU with the dealer fused in: material from op ids op_id .. op_id + 3 (P = 2)."""
+    P = X.shape[0]
+    n = X.numel() // P
+    out = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_private_relu_fused(P, n, _ptr(X), _ptr(out), seed, op_id, _stream()))
+    return out

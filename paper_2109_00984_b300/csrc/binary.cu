@@ -36,6 +36,38 @@ __device__ __forceinline__ Pair and_gate(const Pair& x, const Pair& y, const u64
   return z;
 }
 
+// Where an AND gate's triple comes from: loaded from the dealer's array T
+// [gates][3][2][n], or regenerated in registers from the dealer's own streams
+// (seed, op_id of the AND material): a_p = AND_A(g, p), b_p = AND_B(g, p),
+// c_0 = AND_C(g, 0), c_1 = ((a_0 ^ a_1) & (b_0 ^ b_1)) ^ c_0 -- exactly what
+// mpc_ttp_and_triples writes, so both give bit-identical results.
+struct TripleSrc {
+  const u64* T;  // loaded when non-null
+  u64 seed, op_and;
+  i64 blk;       // Philox block = element quad index
+};
+
+template <bool kGen>
+__device__ __forceinline__ Pair and_gate_src(const Pair& x, const Pair& y, const TripleSrc& src,
+                                             int g, i64 n, i64 i0) {
+  if (!kGen) return and_gate(x, y, src.T, g, n, i0);
+  const u64x4 a0 = prg_block(src.seed, src.op_and, stream_word2(MPC_ROLE_AND_A, g, 0), src.blk);
+  const u64x4 a1 = prg_block(src.seed, src.op_and, stream_word2(MPC_ROLE_AND_A, g, 1), src.blk);
+  const u64x4 b0 = prg_block(src.seed, src.op_and, stream_word2(MPC_ROLE_AND_B, g, 0), src.blk);
+  const u64x4 b1 = prg_block(src.seed, src.op_and, stream_word2(MPC_ROLE_AND_B, g, 1), src.blk);
+  const u64x4 c0 = prg_block(src.seed, src.op_and, stream_word2(MPC_ROLE_AND_C, g, 0), src.blk);
+  Pair z;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const u64 c1 = ((a0.v[j] ^ a1.v[j]) & (b0.v[j] ^ b1.v[j])) ^ c0.v[j];
+    const u64 eps = x.s[0].v[j] ^ a0.v[j] ^ x.s[1].v[j] ^ a1.v[j];
+    const u64 del = y.s[0].v[j] ^ b0.v[j] ^ y.s[1].v[j] ^ b1.v[j];
+    z.s[0].v[j] = c0.v[j] ^ (eps & b0.v[j]) ^ (a0.v[j] & del) ^ (eps & del);
+    z.s[1].v[j] = c1 ^ (eps & b1.v[j]) ^ (a1.v[j] & del);
+  }
+  return z;
+}
+
 __device__ __forceinline__ Pair shl(const Pair& x, int d) {
   Pair o;
 #pragma unroll
@@ -56,7 +88,8 @@ __device__ __forceinline__ Pair xr(const Pair& x, const Pair& y) {
 
 // A2B of arithmetic shares y (already negated for the comparator): binary-share
 // each party's share with the ZERO_BIN streams, then Kogge-Stone add.
-__device__ __forceinline__ Pair a2b_block(const Pair& y, const u64* __restrict__ T, i64 n, i64 i0,
+template <bool kGen>
+__device__ __forceinline__ Pair a2b_block(const Pair& y, const TripleSrc& src, i64 n, i64 i0,
                                           i64 t, u64 seed, u64 op_id) {
   // M_{q,p}: ZERO_BIN stream of owner q, party p.
   const u64x4 m00 = prg_block(seed, op_id, stream_word2(MPC_ROLE_ZERO_BIN, 0, 0), t);
@@ -73,14 +106,14 @@ __device__ __forceinline__ Pair a2b_block(const Pair& y, const u64* __restrict__
     v.s[1].v[j] = m11.v[j] ^ m10.v[j] ^ y.s[1].v[j];
   }
   int gate = 0;
-  Pair G = and_gate(u, v, T, gate++, n, i0);
+  Pair G = and_gate_src<kGen>(u, v, src, gate++, n, i0);
   Pair Pp = xr(u, v);
   const Pair P0 = Pp;
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     const int d = 1 << r;  // 1, 2, 4, 8, 16, 32
-    const Pair Gn = xr(G, and_gate(Pp, shl(G, d), T, gate++, n, i0));
-    if (d < 32) Pp = and_gate(Pp, shl(Pp, d), T, gate++, n, i0);
+    const Pair Gn = xr(G, and_gate_src<kGen>(Pp, shl(G, d), src, gate++, n, i0));
+    if (d < 32) Pp = and_gate_src<kGen>(Pp, shl(Pp, d), src, gate++, n, i0);
     G = Gn;
   }
   return xr(P0, shl(G, 1));
@@ -97,12 +130,18 @@ __global__ void __launch_bounds__(kThreads) a2b_kernel(i64 n, const u64* __restr
     Pair x;
     x.s[0] = load4(X, i0, n);
     x.s[1] = load4(X + n, i0, n);
-    const Pair b = a2b_block(x, T, n, i0, t, seed, op_id);
+    const Pair b = a2b_block<false>(x, TripleSrc{T, 0, 0, t}, n, i0, t, seed, op_id);
     store4(Bout, i0, n, b.s[0]);
     store4(Bout + n, i0, n, b.s[1]);
   }
 }
 
+// Private ReLU for two parties.  kGen = false: the material is read from the
+// dealer's arrays.  kGen = true (fused dealer): it is regenerated in registers
+// from the dealer's streams with op ids op_id (AND triples), op_id + 1 (B2A
+// pairs), op_id + 2 (elementwise triple), and the A2B masks use op_id + 3 --
+// the same words the separate dealer calls would have written.
+template <bool kGen>
 __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64* Y,
                                                         const u64* __restrict__ T,
                                                         const u64* __restrict__ r_arith,
@@ -111,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
                                                         u64 op_id) {
   const i64 nblk = ceil_div(n, 4);
   const i64 nw = ceil_div(n, 64);
+  const u64 op_mask = kGen ? op_id + 3 : op_id;
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
        t += (i64)gridDim.x * blockDim.x) {
     const i64 i0 = 4 * t;
@@ -122,22 +162,60 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
 #pragma unroll
       for (int j = 0; j < 4; ++j) neg.s[p].v[j] = 0ull - x.s[p].v[j];
     // [x > 0] = [(0 - x) < 0]: sign bit of A2B(-x).
-    const Pair sb = a2b_block(neg, T, n, i0, t, seed, op_id);
+    const Pair sb = a2b_block<kGen>(neg, TripleSrc{T, seed, op_id, t}, n, i0, t, seed, op_mask);
     // B2A (Alg. 2): z = reveal(<b> ^ <r>), [b]_p = [r]_p - 2 z [r]_p + [p = 0] z.
-    const int sh = (int)(i0 & 63);
-    const u64 rb0 = r_bin[i0 >> 6] >> sh, rb1 = r_bin[nw + (i0 >> 6)] >> sh;
-    const Quad ra0 = load4(r_arith, i0, n), ra1 = load4(r_arith + n, i0, n);
+    Quad ra0, ra1;
+    u64 rbits;  // bit j = <r>_0 ^ <r>_1 of element i0 + j
+    if (kGen) {
+      const u64x4 r = prg_block(seed, op_id + 1, stream_word2(MPC_ROLE_B2A_R, 0, MPC_TTP_PARTY), t);
+      const u64x4 rb = prg_block(seed, op_id + 1, stream_word2(MPC_ROLE_B2A_BIN, 0, 0), t);
+      const u64x4 rr = prg_block(seed, op_id + 1, stream_word2(MPC_ROLE_B2A_ARITH, 0, 0), t);
+      rbits = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // <r>_1 = r ^ <r>_0, so <r>_0 ^ <r>_1 = r; [r]_1 = r - [r]_0.
+        rbits |= (r.v[j] & 1ull) << j;
+        ra0.v[j] = rr.v[j];
+        ra1.v[j] = (r.v[j] & 1ull) - rr.v[j];
+      }
+    } else {
+      const int sh = (int)(i0 & 63);
+      rbits = (r_bin[i0 >> 6] >> sh) ^ (r_bin[nw + (i0 >> 6)] >> sh);
+      ra0 = load4(r_arith, i0, n);
+      ra1 = load4(r_arith + n, i0, n);
+    }
     Pair bit;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const u64 z = ((sb.s[0].v[j] ^ sb.s[1].v[j]) >> 63) ^ ((rb0 ^ rb1) >> j & 1ull);
+      const u64 z = ((sb.s[0].v[j] ^ sb.s[1].v[j]) >> 63) ^ ((rbits >> j) & 1ull);
       bit.s[0].v[j] = ra0.v[j] - 2ull * z * ra0.v[j] + z;
       bit.s[1].v[j] = ra1.v[j] - 2ull * z * ra1.v[j];
     }
     // Beaver product x * [b] (no truncation: the mask is an unscaled 0/1).
-    const Quad A0 = load4(MT, i0, n), A1 = load4(MT + n, i0, n);
-    const Quad B0 = load4(MT + 2 * n, i0, n), B1 = load4(MT + 3 * n, i0, n);
-    const Quad C0 = load4(MT + 4 * n, i0, n), C1 = load4(MT + 5 * n, i0, n);
+    Quad A0, A1, B0, B1, C0, C1;
+    if (kGen) {
+      const u64x4 a0 = prg_block(seed, op_id + 2, stream_word2(MPC_ROLE_TRIPLE_A, 0, 0), t);
+      const u64x4 a1 = prg_block(seed, op_id + 2, stream_word2(MPC_ROLE_TRIPLE_A, 0, 1), t);
+      const u64x4 b0 = prg_block(seed, op_id + 2, stream_word2(MPC_ROLE_TRIPLE_B, 0, 0), t);
+      const u64x4 b1 = prg_block(seed, op_id + 2, stream_word2(MPC_ROLE_TRIPLE_B, 0, 1), t);
+      const u64x4 c0 = prg_block(seed, op_id + 2, stream_word2(MPC_ROLE_TRIPLE_C, 0, 0), t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        A0.v[j] = a0.v[j];
+        A1.v[j] = a1.v[j];
+        B0.v[j] = b0.v[j];
+        B1.v[j] = b1.v[j];
+        C0.v[j] = c0.v[j];
+        C1.v[j] = (a0.v[j] + a1.v[j]) * (b0.v[j] + b1.v[j]) - c0.v[j];
+      }
+    } else {
+      A0 = load4(MT, i0, n);
+      A1 = load4(MT + n, i0, n);
+      B0 = load4(MT + 2 * n, i0, n);
+      B1 = load4(MT + 3 * n, i0, n);
+      C0 = load4(MT + 4 * n, i0, n);
+      C1 = load4(MT + 5 * n, i0, n);
+    }
     Quad y0, y1;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -390,10 +468,31 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
   int rc;
   {
     KernelTimer timer("private_relu", as_stream(stream));
-    relu_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, as_stream(stream)>>>(
+    relu_kernel<false><<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, as_stream(stream)>>>(
         n, (const u64*)X, (u64*)Y, (const u64*)and_triples, (const u64*)r_arith,
         (const u64*)r_bin, (const u64*)mul_triple, seed, op_id);
     rc = check_launch("private_relu");
+  }
+  if (rc == MPC_OK)
+    stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,
+              (uint64_t)MPC_KS_GATES * n, (uint64_t)MPC_KS_GATES * 6ull * n + 2ull * n + 6ull * n,
+              0);
+  return rc;
+}
+
+int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
+                           uint64_t op_id, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "fused private ReLU supports P = 2 (got %d)", P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(X && Y, "null pointer");
+  int rc;
+  {
+    KernelTimer timer("private_relu_fused", as_stream(stream));
+    relu_kernel<true><<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, as_stream(stream)>>>(
+        n, (const u64*)X, (u64*)Y, nullptr, nullptr, nullptr, nullptr, seed, op_id);
+    rc = check_launch("private_relu_fused");
   }
   if (rc == MPC_OK)
     stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,

@@ -20,6 +20,21 @@ struct GemmJob {
   u64* Z;
 };
 
+// Implicit im2col for the B operand of a convolution (limb engine only): the
+// (k, n) element of B1 is sum_{q < n1} (src1 - sub1)[q * stride1 + pos(k, n)]
+// and that of B2 for job j is src2[j][pos(k, n)], where pos is the data
+// position of kernel tap k = (ci, r, s) for output column n = (b, oh, ow),
+// and the element is 0 in the padding.  sub1 may be null.
+struct ConvGather {
+  mpc_conv_desc d;
+  i64 ho, wo;
+  const u64* src1;
+  const u64* sub1;
+  i64 stride1;
+  int n1;
+  const u64* src2[MPC_MAX_PARTIES];
+};
+
 // splits > 1 partitions the (pair-concatenated) K range over `splits` CTAs per
 // output tile; each writes its raw partial sum to partial[split][job][M][N]
 // and gemm_reduce() forms Z = trunc(C + sum of partials) (exact mod 2^64).
@@ -30,6 +45,7 @@ struct GemmArgs {
   int njobs;
   int splits;
   u64* partial;
+  const ConvGather* gather;  // host pointer; when set, B1/B2 are implicit im2col (limb only)
   GemmJob jobs[MPC_MAX_PARTIES];
 };
 

@@ -513,6 +513,65 @@ __global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
   }
 }
 
+// B side of a convolution, gathered straight from the data (implicit im2col):
+// the same tiling and stores as limb_planes_b, with element (k', n) read at its
+// data position instead of from a materialised im2col matrix.
+__global__ void __launch_bounds__(256) limb_planes_b_conv(const ConvGather cg, int job,
+                                                           __nv_bfloat16* out, i64 N, i64 K,
+                                                           i64 Kp) {
+  __shared__ uint32_t tile[8][PB_TN][PB_ROW];
+  const mpc_conv_desc& d = cg.d;
+  const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
+  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
+  const i64 n = n0 + nl;
+  // Output column n -> (b, oh, ow).
+  const i64 ow = n % cg.wo, oh = (n / cg.wo) % cg.ho, b = n / (cg.wo * cg.ho);
+  const u64* src2 = cg.src2[job];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int kl = 2 * (kq + 8 * j);
+    u64 v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      i64 k = k0 + kl + e;
+      v[e] = 0;
+      const bool first = k < K;
+      if (!first) k -= K;
+      if (n < N && k < K && (first || src2)) {
+        const i64 s_ = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
+        const i64 y = oh * d.stride_h + r - d.pad_h, x = ow * d.stride_w + s_ - d.pad_w;
+        if (y >= 0 && y < d.h && x >= 0 && x < d.w) {
+          const i64 off = ((b * d.c_in + ci) * d.h + y) * d.w + x;
+          if (first) {
+            u64 acc = 0;
+            for (int q = 0; q < cg.n1; ++q) {
+              acc += cg.src1[q * cg.stride1 + off];
+              if (cg.sub1) acc -= cg.sub1[q * cg.stride1 + off];
+            }
+            v[e] = acc;
+          } else {
+            v[e] = src2[off];
+          }
+        }
+      }
+    }
+    int d0[8], d1[8];
+    balanced_digits(v[0], d0);
+    balanced_digits(v[1], d1);
+#pragma unroll
+    for (int pl = 0; pl < 8; ++pl) tile[pl][nl][kl >> 1] = pack_bf16x2(d0[pl], d1[pl]);
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int r = warp; r < 8 * PB_TN; r += 8) {
+    const int pl = r / PB_TN, row = r % PB_TN;
+    const i64 nn = n0 + row;
+    const i64 kk = k0 + 2 * lane;
+    if (nn < N && kk < Kp)
+      *reinterpret_cast<uint32_t*>(out + ((i64)pl * N + nn) * Kp + kk) = tile[pl][row][lane];
+  }
+}
+
 // ---- host side -----------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -610,9 +669,17 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     limb_planes_a<<<ga, 256, 0, s>>>(ja[0], ja[1], ja[2], ja[3], ja[4], ja[5], ja[6],
                                      ja[7], g.M, g.K, Kp);
     if (int rc = check_launch("limb_planes_a")) return rc;
-    limb_planes_b<<<gb, 256, 0, s>>>(jbv[0], jbv[1], jbv[2], jbv[3], jbv[4], jbv[5],
-                                     jbv[6], jbv[7], g.N, g.K, Kp);
-    if (int rc = check_launch("limb_planes_b")) return rc;
+    if (g.gather) {
+      for (int j = 0; j < g.njobs; ++j) {
+        dim3 gj(gb.x, gb.y, 1);
+        limb_planes_b_conv<<<gj, 256, 0, s>>>(*g.gather, j, jbv[j].out, g.N, g.K, Kp);
+        if (int rc = check_launch("limb_planes_b_conv")) return rc;
+      }
+    } else {
+      limb_planes_b<<<gb, 256, 0, s>>>(jbv[0], jbv[1], jbv[2], jbv[3], jbv[4], jbv[5],
+                                       jbv[6], jbv[7], g.N, g.K, Kp);
+      if (int rc = check_launch("limb_planes_b")) return rc;
+    }
   }
   prm.M = g.M;
   prm.N = g.N;

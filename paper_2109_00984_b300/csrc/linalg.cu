@@ -201,10 +201,12 @@ size_t matmul_ws(int P, i64 M, i64 N, i64 K, int algo) {
   return align256(words(M * K)) + 2 * align256(words(K * N)) + engine_ws(algo, M, N, K, 2, P);
 }
 
+// The limb engine gathers im2col straight into its digit planes, so only the
+// plain engine needs the materialised im2col(E) and im2col(A_p).
 size_t conv_ws(int P, const mpc_conv_desc& d, i64 ho, i64 wo, int algo) {
   const i64 M = d.c_out, K = d.c_in * d.kh * d.kw, N = d.batch * ho * wo;
-  return (size_t)(P + 1) * align256(words(K * N)) + 2 * align256(words(M * K)) +
-         engine_ws(algo, M, N, K, 2, P);
+  const size_t cols = algo == MPC_ALGO_LIMB ? 0 : (size_t)(P + 1) * align256(words(K * N));
+  return cols + 2 * align256(words(M * K)) + engine_ws(algo, M, N, K, 2, P);
 }
 
 size_t matmul_triple_ws(i64 M, i64 N, i64 K, int algo) {
@@ -214,8 +216,8 @@ size_t matmul_triple_ws(i64 M, i64 N, i64 K, int algo) {
 size_t conv_triple_ws(const mpc_conv_desc& d, i64 ho, i64 wo, int algo) {
   const i64 M = d.c_out, K = d.c_in * d.kh * d.kw, N = d.batch * ho * wo;
   const i64 nx = d.batch * d.c_in * d.h * d.w;
-  return align256(words(nx)) + align256(words(K * N)) + align256(words(M * K)) +
-         engine_ws(algo, M, N, K, 1, 1);
+  const size_t cols = algo == MPC_ALGO_LIMB ? 0 : align256(words(K * N));
+  return align256(words(nx)) + cols + align256(words(M * K)) + engine_ws(algo, M, N, K, 1, 1);
 }
 
 int check_algo(int algo) {
@@ -314,18 +316,36 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
   if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
   cudaStream_t s = as_stream(stream);
   Carve cv(ws);
-  u64* Ecol = cv.take(K * N);
-  u64* Acol[MPC_MAX_PARTIES];
-  for (int p = 0; p < P; ++p) Acol[p] = cv.take(K * N);
+  const bool gather = algo == MPC_ALGO_LIMB;
+  u64* Ecol = nullptr;
+  u64* Acol[MPC_MAX_PARTIES] = {nullptr};
+  if (!gather) {
+    Ecol = cv.take(K * N);
+    for (int p = 0; p < P; ++p) Acol[p] = cv.take(K * N);
+  }
   u64* F = cv.take(M * K);
   u64* G = cv.take(M * K);
-  // E = sum_p (X_p - A_p) gathered straight into im2col layout.
-  if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)X, (const u64*)A, nx, P}, Ecol, s))
-    return rc;
-  for (int p = 0; p < P; ++p)
-    if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)A + p * nx, nullptr, nx, 1},
-                               Acol[p], s))
+  ConvGather cg{};
+  if (gather) {
+    // The limb engine reads E = sum_p (X_p - A_p) and A_p at their data positions.
+    cg.d = *d;
+    cg.ho = ho;
+    cg.wo = wo;
+    cg.src1 = (const u64*)X;
+    cg.sub1 = (const u64*)A;
+    cg.stride1 = nx;
+    cg.n1 = P;
+    for (int p = 0; p < P; ++p) cg.src2[p] = (const u64*)A + p * nx;
+  } else {
+    // E = sum_p (X_p - A_p) gathered straight into im2col layout.
+    if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)X, (const u64*)A, nx, P}, Ecol,
+                               s))
       return rc;
+    for (int p = 0; p < P; ++p)
+      if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{(const u64*)A + p * nx, nullptr, nx, 1},
+                                 Acol[p], s))
+        return rc;
+  }
   MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
   if (int rc = check_launch("open F")) return rc;
   GemmArgs g{};
@@ -335,6 +355,7 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
   g.hw_out = ho * wo;
   g.trunc_bits = trunc_bits;
   g.njobs = P;
+  g.gather = gather ? &cg : nullptr;
   for (int p = 0; p < P; ++p) {
     g.jobs[p].A1 = p == 0 ? G : (const u64*)B + (i64)p * M * K;
     g.jobs[p].B1 = Ecol;
@@ -450,8 +471,9 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
   cudaStream_t s = as_stream(stream);
   Carve cv(ws);
+  const bool gather = algo == MPC_ALGO_LIMB;
   u64* a = cv.take(nx);
-  u64* acol = cv.take(K * N);
+  u64* acol = gather ? nullptr : cv.take(K * N);
   u64* b = cv.take(M * K);
   fill_sum_kernel<<<grid_for(ceil_div(nx, 4), kThreads), kThreads, 0, s>>>(
       P, nx, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a);
@@ -459,7 +481,16 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   fill_sum_kernel<<<grid_for(ceil_div(M * K, 4), kThreads), kThreads, 0, s>>>(
       P, M * K, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b);
   if (int rc = check_launch("fill B")) return rc;
-  if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{a, nullptr, 0, 1}, acol, s)) return rc;
+  ConvGather cg{};
+  if (gather) {
+    cg.d = *d;
+    cg.ho = ho;
+    cg.wo = wo;
+    cg.src1 = a;
+    cg.n1 = 1;
+  } else if (int rc = launch_im2col(*d, ho, wo, Im2colSrc{a, nullptr, 0, 1}, acol, s)) {
+    return rc;
+  }
   u64* Clast = (u64*)C + (i64)(P - 1) * M * N;
   GemmArgs g{};
   g.M = M;
@@ -467,6 +498,7 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   g.K = K;
   g.hw_out = ho * wo;
   g.njobs = 1;
+  g.gather = gather ? &cg : nullptr;
   g.jobs[0] = GemmJob{b, acol, nullptr, nullptr, nullptr, Clast};
   if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s)) return rc;
   share_product_kernel<<<grid_for(ceil_div(M * N, 4), kThreads), kThreads, 0, s>>>(

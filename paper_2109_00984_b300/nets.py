@@ -4,6 +4,10 @@ Each layer runs, on the device and through the C ABI only:
   dealer:  ttp_conv2d_triple, ttp_and_triples, ttp_b2a_bits, ttp_mul_triple
   online:  beaver_conv2d (+ truncation by 2^16 fused in its epilogue),
            private_relu (A2B + Kogge-Stone + B2A + Beaver mask product)
+With fused_relu (the default) the four ReLU dealer calls and private_relu are
+one private_relu_fused call that regenerates the same material in registers
+(bit-identical results; the schedule's and/b2a/mul/relu op ids are
+consecutive).
 The weights are shared once by party 1 at construction; the input is shared by
 party 0 in every forward, and the output is revealed at the end (§5.1, §5.2).
 All buffers are allocated up front so that a forward can be captured in a
@@ -16,8 +20,9 @@ from . import api
 
 class PrivateConv1dStack:
     def __init__(self, weights, strides, pads, frames, batch=1, algo=api.PLAIN, frac_bits=16,
-                 weight_ops=None, seed=1, device="cuda"):
+                 weight_ops=None, seed=1, device="cuda", fused_relu=True):
         self.P = 2
+        self.fused_relu = fused_relu
         self.algo = algo
         self.frac_bits = frac_bits
         self.seed = seed
@@ -51,14 +56,15 @@ class PrivateConv1dStack:
                 C=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
                 Z=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
                 Y=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
-                T=torch.empty((api.KS_GATES, 3, P, n), dtype=torch.int64, device=dev),
-                ra=torch.empty((P, n), dtype=torch.int64, device=dev),
-                rb=torch.empty((P, (n + 63) // 64), dtype=torch.int64, device=dev),
-                MT=torch.empty((3, P, n), dtype=torch.int64, device=dev),
                 n=n,
             )
             ws_bytes = max(ws_bytes, api.conv2d_workspace_size(P, d, self.algo),
                            api.conv2d_triple_workspace_size(P, d, self.algo))
+            if not self.fused_relu:
+                b.update(T=torch.empty((api.KS_GATES, 3, P, n), dtype=torch.int64, device=dev),
+                         ra=torch.empty((P, n), dtype=torch.int64, device=dev),
+                         rb=torch.empty((P, (n + 63) // 64), dtype=torch.int64, device=dev),
+                         MT=torch.empty((3, P, n), dtype=torch.int64, device=dev))
             self.bufs.append(b)
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
@@ -76,11 +82,17 @@ class PrivateConv1dStack:
             api.beaver_conv2d(X, self.W[l], b["A"], b["B"], b["C"], d, self.algo,
                               trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)
             n = b["n"]
-            api.ttp_and_triples(self.P, n, seed, ops["and"], out=b["T"])
-            api.ttp_b2a_bits(self.P, n, seed, ops["b2a"], out=(b["ra"], b["rb"]))
-            MT = b["MT"]
-            api.ttp_mul_triple(self.P, n, seed, ops["mul"], out=(MT[0], MT[1], MT[2]))
-            api.private_relu(b["Z"], b["T"], b["ra"], b["rb"], MT, seed, ops["relu"], out=b["Y"])
+            if self.fused_relu:
+                assert (ops["b2a"], ops["mul"], ops["relu"]) == (ops["and"] + 1, ops["and"] + 2,
+                                                                 ops["and"] + 3)
+                api.private_relu_fused(b["Z"], seed, ops["and"], out=b["Y"])
+            else:
+                api.ttp_and_triples(self.P, n, seed, ops["and"], out=b["T"])
+                api.ttp_b2a_bits(self.P, n, seed, ops["b2a"], out=(b["ra"], b["rb"]))
+                MT = b["MT"]
+                api.ttp_mul_triple(self.P, n, seed, ops["mul"], out=(MT[0], MT[1], MT[2]))
+                api.private_relu(b["Z"], b["T"], b["ra"], b["rb"], MT, seed, ops["relu"],
+                                 out=b["Y"])
             X = b["Y"]
         return X
 

@@ -12,7 +12,8 @@ the material and the online calls consume it:
   global average pool:   global_avgpool (local sum, floor division by H*W)
 Material op_ids follow the schedule: a layer op with id `op` uses op (triple /
 AND triples), op+1 (B2A bits), op+2 (ReLU's elementwise triple), op+3 (A2B
-masks).
+masks).  With fused_relu (the default) each ReLU is one private_relu_fused
+call regenerating that material in registers (bit-identical results).
 """
 import torch
 
@@ -20,8 +21,10 @@ from . import api
 
 
 class PrivateResNet18:
-    def __init__(self, weights, layers, schedule, algo=api.AUTO, frac_bits=16, device="cuda"):
+    def __init__(self, weights, layers, schedule, algo=api.AUTO, frac_bits=16, device="cuda",
+                 fused_relu=True):
         self.P = 2
+        self.fused_relu = fused_relu
         self.layers = layers
         self.algo = algo
         self.frac_bits = frac_bits
@@ -53,6 +56,8 @@ class PrivateResNet18:
         P = X.shape[0]
         flat = X.reshape(P, -1)
         n = flat.shape[1]
+        if self.fused_relu:
+            return api.private_relu_fused(flat, self.seed, op).view(X.shape)
         T = api.ttp_and_triples(P, n, self.seed, op, device=self.device)
         ra, rb = api.ttp_b2a_bits(P, n, self.seed, op + 1, device=self.device)
         MT = torch.empty((3, P, n), dtype=torch.int64, device=self.device)

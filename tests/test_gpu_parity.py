@@ -344,3 +344,18 @@ def test_private_relu_adder_tree(mpc, P, rng):
     got = host(mpc.private_relu(dev(X), dev(T), gra, grb, tuple(dev(t) for t in mt), SEED, 99))
     assert np.array_equal(got, binary.private_relu(X, T, ra, rb, mt, SEED, 99))
     assert sharing.reveal(got).view(np.int64).tolist() == np.maximum(v, 0).tolist()
+
+
+@pytest.mark.parametrize("n", [1, 7, 4096, 65 * 64 + 3, 200001])
+def test_private_relu_fused_dealer(mpc, n, rng):
+    """Dealer regenerated in registers: identical to the separate dealer calls."""
+    v = rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)
+    v[: min(3, n)] = [0, 1, -1][: min(3, n)]
+    X = sharing.share(v.view(np.uint64), 2, 0, SEED, 61)
+    op = 700
+    T = dealer.and_triples(2, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(2, n, SEED, op + 1)
+    mt = dealer.mul_triple(2, n, SEED, op + 2)
+    ref = binary.private_relu(X, T, ra, rb, mt, SEED, op + 3)
+    got = host(mpc.private_relu_fused(dev(X), SEED, op))
+    assert np.array_equal(got, ref)

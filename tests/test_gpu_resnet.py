@@ -55,17 +55,20 @@ def test_maxpool_tree(mpc, rng):
     from paper_2109_00984_b300.resnet import PrivateResNet18
     v = rng.integers(0, 1 << 40, (2, 4, 11, 10)).astype(np.int64)
     X = sharing.share(v.view(np.uint64), 2, 0, 1, 3)
-    net = PrivateResNet18({}, [], synth.resnet_schedule())
+    net = PrivateResNet18({}, [], synth.resnet_schedule(), fused_relu=False)
     got = host(net.maxpool(dev(X), 3, 2, 1, [101, 111, 121, 131]))
+    net_f = PrivateResNet18({}, [], synth.resnet_schedule(), fused_relu=True)
+    assert np.array_equal(host(net_f.maxpool(dev(X), 3, 2, 1, [101, 111, 121, 131])), got)
     ref = oresnet.maxpool_shares(X, 3, 2, 1, [101, 111, 121, 131], 1)
     assert np.array_equal(got, ref)
 
 
-def _gpu_forward(mpc, x, algo=None):
+def _gpu_forward(mpc, x, algo=None, fused=True):
     from paper_2109_00984_b300.resnet import PrivateResNet18
     W = synth.resnet_weights()
     sched = synth.resnet_schedule()
-    net = PrivateResNet18(W, synth.RESNET18, sched, algo=mpc.AUTO if algo is None else algo)
+    net = PrivateResNet18(W, synth.RESNET18, sched, algo=mpc.AUTO if algo is None else algo,
+                          fused_relu=fused)
     Y = net.forward(dev_f64(x), sched)
     real = net.reveal(Y)
     torch.cuda.synchronize()
@@ -80,10 +83,10 @@ def _oracle_forward(x):
     return shares, real, W
 
 
-@pytest.mark.parametrize("engine", ["plain", "auto"])
-def test_small_resnet_bit_exact(mpc, engine):
+@pytest.mark.parametrize("engine,fused", [("plain", False), ("auto", True)])
+def test_small_resnet_bit_exact(mpc, engine, fused):
     x = synth.resnet_input(batch=2, hw=32)
-    got, got_real = _gpu_forward(mpc, x, mpc.PLAIN if engine == "plain" else mpc.AUTO)
+    got, got_real = _gpu_forward(mpc, x, mpc.PLAIN if engine == "plain" else mpc.AUTO, fused)
     ref, ref_real, _ = _oracle_forward(x)
     assert np.array_equal(got, ref)
     assert np.array_equal(got_real, ref_real)

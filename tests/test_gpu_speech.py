@@ -26,11 +26,11 @@ def mpc():
     return m
 
 
-def _run(mpc, x, ws, strides, pads, algo, step=0):
+def _run(mpc, x, ws, strides, pads, algo, step=0, fused=True):
     from paper_2109_00984_b300.nets import PrivateConv1dStack
     sched = synth.speech_schedule(len(ws), step=step)
     net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=algo,
-                             weight_ops=sched["weight_op"], seed=sched["seed"])
+                             weight_ops=sched["weight_op"], seed=sched["seed"], fused_relu=fused)
     Y = net.forward(dev_f64(x), sched)
     real = net.reveal(Y)
     torch.cuda.synchronize()
@@ -42,10 +42,10 @@ def _oracle(x, ws, strides, pads, sched):
     return nets.private_conv1d_stack(x, Wsh, strides, pads, sched, return_shares=True)
 
 
-@pytest.mark.parametrize("step", [0, 3])
-def test_small_stack_bit_exact(mpc, step):
+@pytest.mark.parametrize("step,fused", [(0, False), (3, False), (0, True)])
+def test_small_stack_bit_exact(mpc, step, fused):
     x, ws, strides, pads = synth.speech_small()
-    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, mpc.PLAIN, step)
+    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, mpc.PLAIN, step, fused)
     ref_real, ref_shares = _oracle(x, ws, strides, pads, sched)
     assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     assert np.array_equal(got_real.reshape(ref_real.shape), ref_real)
@@ -63,10 +63,10 @@ def full_oracle():
 @pytest.mark.slow
 @pytest.mark.parametrize("engine", ["plain", "auto"])
 def test_full_speech_stack_bit_exact(mpc, full_oracle, engine):
-    """Full stack in bench.py's configuration (engine AUTO = limb for these shapes)."""
+    """Full stack; "auto" is bench.py's configuration (limb engine, fused-dealer ReLU)."""
     x, ws, strides, pads = synth.speech_stack()
     algo = mpc.PLAIN if engine == "plain" else mpc.AUTO
-    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, algo)
+    got_shares, got_real, sched = _run(mpc, x, ws, strides, pads, algo, fused=(engine == "auto"))
     ref_shares, plain = full_oracle
     assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
