@@ -58,6 +58,26 @@ def dist_env():
     return rank, world, local
 
 
+def job_time(local_s, world, device=None):
+    """Max over ranks of a per-rank duration (the slowest replica sets the pace).
+
+    Replicas share nothing on the data path; this reduction is the only
+    collective, used for timing only.
+    """
+    if world <= 1:
+        return float(local_s)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, slowest_s):
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return world * units_per_rank / slowest_s
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -229,12 +249,8 @@ def run_ours(args):
     prof = {k: mpc.profile_read(k) for k in ("gemm_plain", "gemm_limb", "limb_planes",
                                                  "private_relu", "private_relu_fused")}
     total_ms = float(sum(step_ms))
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max = job_time(total_ms, world, dev)
+    value = whole_job_rate(args.steps, world, t_max / 1e3)
 
     # ---- end to end through the public API with pinned host buffers ------
     x_host = torch.from_numpy(x).pin_memory()
@@ -255,12 +271,9 @@ def run_ours(args):
         out_host.copy_(out, non_blocking=True)
     e_stop.record(stream)
     torch.cuda.synchronize()
-    e2e_s = max(time.perf_counter() - t0, e_start.elapsed_time(e_stop) / 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "samples/s",
+    e2e_s = job_time(max(time.perf_counter() - t0, e_start.elapsed_time(e_stop) / 1e3), world,
+                     dev)
+    e2e = {"value": whole_job_rate(e2e_steps, world, e2e_s), "unit": "samples/s",
            "h2d_bytes_per_step": int(x_host.numel() * 8),
            "d2h_bytes_per_step": int(out_host.numel() * 8)}
 

@@ -31,8 +31,11 @@ __device__ __forceinline__ u64x4 philox4x64_10(u64 c0, u64 c1, u64 c2, u64 c3, u
       k0 += kPhiloxW0;
       k1 += kPhiloxW1;
     }
-    const u64 hi0 = __umul64hi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
-    const u64 hi1 = __umul64hi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+    // One full 64x64 -> 128-bit product per multiplier gives both halves.
+    const unsigned __int128 p0 = (unsigned __int128)kPhiloxM0 * c0;
+    const unsigned __int128 p1 = (unsigned __int128)kPhiloxM1 * c2;
+    const u64 hi0 = (u64)(p0 >> 64), lo0 = (u64)p0;
+    const u64 hi1 = (u64)(p1 >> 64), lo1 = (u64)p1;
     const u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
