@@ -328,6 +328,34 @@ int mpc_truncate_nparty(int P, int64_t n, uint64_t* shares, const uint64_t* r,
 int mpc_ttp_trunc_pairs(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* r,
                         uint64_t* theta_r, void* stream);
 
+/* Beaver square (App. D.1.1 "Square"): with a pair ([a], [b]), b = a^2, open
+ * eps = sum_p (X_p - A_p) in registers and write Z_p = B_p + 2 eps A_p
+ * (+ eps^2 on party 0), then optionally s(Z_p) >> trunc_bits.  One round.
+ * X, A, B, Z device u64 [P][n]; Z may alias X. */
+int mpc_beaver_square(int P, int64_t n, const uint64_t* X, const uint64_t* A, const uint64_t* B,
+                      uint64_t* Z, int trunc_bits, void* stream);
+
+/* Dealer pair for mpc_beaver_square: A[p] = stream(TRIPLE_A, p), b = a^2
+ * shared as B[p] = stream(TRIPLE_C, p) for p < P-1 and the correction on P-1. */
+int mpc_ttp_square_pair(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* A, uint64_t* B,
+                        void* stream);
+
+/* [x < 0] (§5.2 "Comparators"): B2A(MSB(A2B([x]))) as arithmetic shares of an
+ * unscaled 0/1 bit, Out device u64 [P][n].  Material as for mpc_private_relu
+ * without the elementwise triple: and_triples [12 (P-1)][3][P][n], r_arith,
+ * r_bin from mpc_ttp_b2a_bits; (seed, op_id) drive the A2B masks.  The other
+ * comparators follow: [x < y] = [x - y < 0], [x > y] = [y - x < 0],
+ * [x >= y] = 1 - [x < y], [x <= y] = 1 - [x > y], [x == y] = [x <= y] - [x < y]. */
+int mpc_ltz(int P, int64_t n, const uint64_t* X, uint64_t* out, const uint64_t* and_triples,
+            const uint64_t* r_arith, const uint64_t* r_bin, uint64_t seed, uint64_t op_id,
+            void* stream);
+
+/* Public affine map, local (§5.2): Z_p = scale * X_p, plus `offset` (a public
+ * ring element) on party 0, then if trunc_bits > 0 the two-party local
+ * truncation s(Z_p) >> trunc_bits.  Z may alias X. */
+int mpc_affine(int P, int64_t n, const uint64_t* X, uint64_t* Z, int64_t scale, uint64_t offset,
+               int trunc_bits, void* stream);
+
 /* ---- local share operations (no communication) --------------------------- */
 
 /* Private addition / subtraction (§5.2 "Private addition"): Z_p = X_p + Y_p

@@ -57,3 +57,30 @@ def beaver_conv2d(X, W, A, B, C, stride, pad, pad_w=None, tr=None):
     """X [P][N][Cin][H][W] (data), W [P][Cout][Cin][kh][kw] (weights)."""
     f = lambda x, w: ring.conv2d(x, w, stride=stride, pad=pad, pad_w=pad_w)
     return beaver(X, W, A, B, C, f, tr)[0]
+
+
+def beaver_square(X, A, B, tr=None):
+    """App. D.1.1 "Square": open eps = x - a, [x^2] = [b] + 2 eps [a] + eps^2 (party 0)."""
+    tr = _maybe(tr)
+    X, A, B = (np.asarray(t, dtype=U64) for t in (X, A, B))
+    with np.errstate(over="ignore"):
+        eps = reveal(X - A)
+        tr.open(eps.nbytes)
+        tr.next_round()
+        Z = B + U64(2) * eps[None] * A
+        Z[0] += eps * eps
+    return Z
+
+
+def affine(X, scale, offset=0, trunc_bits=0):
+    """Local: Z_p = scale * X_p (+ offset on party 0), then optional two-party truncation.
+
+    scale is a public integer and offset a public ring element (§5.2: products
+    and sums with public values are local).
+    """
+    from .truncation import truncate
+    X = np.asarray(X, dtype=U64)
+    with np.errstate(over="ignore"):
+        Z = X * U64(int(scale) % (1 << 64))
+        Z[0] += U64(int(offset) % (1 << 64))
+    return truncate(Z, trunc_bits) if trunc_bits else Z

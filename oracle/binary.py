@@ -161,3 +161,9 @@ def private_relu(x, and_triples, r_arith, r_bin, mul_triple, seed, op_id, tr=Non
     mask = gt_zero(x, and_triples, r_arith, r_bin, seed, op_id, tr)
     A, B, C = mul_triple
     return beaver_mul(x, mask, A, B, C, tr)
+
+
+def ltz(x, and_triples, r_arith, r_bin, seed, op_id, tr=None):
+    """[x < 0] = B2A(MSB(A2B([x]))) (§5.2 "Comparators"), arithmetic 0/1 shares."""
+    b = a2b(np.asarray(x, dtype=U64), and_triples, seed, op_id, tr)
+    return b2a_bit(msb(b), r_arith, r_bin, tr)

@@ -133,3 +133,16 @@ def trunc_pairs(P, n, seed, op_id):
             acc += TH[p]
         TH[P - 1] = th - acc
     return R, TH
+
+
+def square_pair(P, n, seed, op_id):
+    """Beaver pair ([a], [b]) with b = a^2 (App. D.1.1 "Square").
+
+    A_p = TRIPLE_A words for all p; b's shares are TRIPLE_C words for p < P-1
+    and the correction on party P-1.  Returns (A, B) each [P][n].
+    """
+    A = _streams(P, prg.TRIPLE_A, 0, n, seed, op_id)
+    with np.errstate(over="ignore"):
+        a = reveal(A)
+        b = a * a
+    return A, _share_product(b, P, prg.TRIPLE_C, 0, seed, op_id)

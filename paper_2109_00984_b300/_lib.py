@@ -74,6 +74,10 @@ SIGNATURES = {
     "mpc_ring_gemm_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_int]),
     "mpc_ring_gemm": (c_int, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp, c_size,
                               c_vp]),
+    "mpc_beaver_square": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp]),
+    "mpc_ttp_square_pair": (c_int, [c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
+    "mpc_ltz": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64, c_vp]),
+    "mpc_affine": (c_int, [c_int, c_i64, c_vp, c_vp, c_i64, c_u64, c_int, c_vp]),
     "mpc_private_relu_fused": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_vp]),
     "mpc_truncate_nparty": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_int, c_vp]),
     "mpc_ttp_trunc_pairs": (c_int, [c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),

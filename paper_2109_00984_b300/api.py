@@ -422,3 +422,73 @@ def private_relu_fused(X, seed, op_id, out=None):
     out = torch.empty_like(X) if out is None else out
     _check(_L().mpc_private_relu_fused(P, n, _ptr(X), _ptr(out), seed, op_id, _stream()))
     return out
+
+
+# ---- square, comparators, multiplexing ----------------------------------------------
+def ttp_square_pair(P, n, seed, op_id, device="cuda", out=None):
+    A, B = out if out is not None else (_words((P, n), device), _words((P, n), device))
+    _check(_L().mpc_ttp_square_pair(P, n, seed, op_id, _ptr(A), _ptr(B), _stream()))
+    return A, B
+
+
+def beaver_square(X, A, B, trunc_bits=0, out=None):
+    P = X.shape[0]
+    Z = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_beaver_square(P, X.numel() // P, _ptr(X), _ptr(A), _ptr(B), _ptr(Z), trunc_bits,
+                                  _stream()))
+    return Z
+
+
+def affine(X, scale, offset=0, trunc_bits=0, out=None):
+    """Z_p = scale * X_p (+ offset on party 0), optional two-party truncation."""
+    P = X.shape[0]
+    Z = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_affine(P, X.numel() // P, _ptr(X), _ptr(Z), int(scale),
+                           int(offset) % (1 << 64), trunc_bits, _stream()))
+    return Z
+
+
+def ltz(X, seed, op_id, out=None):
+    """[x < 0] as unscaled 0/1 shares; material at op_id, op_id + 1, masks at op_id + 3."""
+    P = X.shape[0]
+    n = X.numel() // P
+    T = ttp_and_triples(P, n, seed, op_id, gates=KS_GATES * (P - 1), device=X.device)
+    ra, rb = ttp_b2a_bits(P, n, seed, op_id + 1, device=X.device)
+    out = torch.empty_like(X) if out is None else out
+    _check(_L().mpc_ltz(P, n, _ptr(X), _ptr(out), _ptr(T), _ptr(ra), _ptr(rb), seed, op_id + 3,
+                        _stream()))
+    return out
+
+
+def lt(X, Y, seed, op_id):
+    return ltz(sub(X, Y), seed, op_id)
+
+
+def gt(X, Y, seed, op_id):
+    return ltz(sub(Y, X), seed, op_id)
+
+
+def ge(X, Y, seed, op_id):
+    return affine(lt(X, Y, seed, op_id), -1, 1)
+
+
+def le(X, Y, seed, op_id):
+    return affine(gt(X, Y, seed, op_id), -1, 1)
+
+
+def eq(X, Y, seed, op_id):
+    """[x <= y] - [x < y]; the two comparisons use op_id and op_id + 10."""
+    return sub(le(X, Y, seed, op_id), lt(X, Y, seed, op_id + 10))
+
+
+def ne(X, Y, seed, op_id):
+    return affine(eq(X, Y, seed, op_id), -1, 1)
+
+
+def mux(C, X, Y, seed, op_id):
+    """[c ? x : y] = [c] ([x] - [y]) + [y] with the elementwise triple at op_id."""
+    P = C.shape[0]
+    n = C.numel() // P
+    A, B, T = ttp_mul_triple(P, n, seed, op_id, device=C.device)
+    prod = beaver_mul(C, sub(X, Y), A.view(C.shape), B.view(C.shape), T.view(C.shape))
+    return add(prod, Y)

@@ -229,6 +229,36 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
   }
 }
 
+// [x < 0] for two parties: A2B of x (no negation), sign bit, B2A (Alg. 2).
+__global__ void __launch_bounds__(kThreads) ltz_kernel(i64 n, const u64* X, u64* Out,
+                                                       const u64* __restrict__ T,
+                                                       const u64* __restrict__ r_arith,
+                                                       const u64* __restrict__ r_bin, u64 seed,
+                                                       u64 op_id) {
+  const i64 nblk = ceil_div(n, 4);
+  const i64 nw = ceil_div(n, 64);
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
+       t += (i64)gridDim.x * blockDim.x) {
+    const i64 i0 = 4 * t;
+    Pair x;
+    x.s[0] = load4(X, i0, n);
+    x.s[1] = load4(X + n, i0, n);
+    const Pair sb = a2b_block<false>(x, TripleSrc{T, 0, 0, t}, n, i0, t, seed, op_id);
+    const int sh = (int)(i0 & 63);
+    const u64 rbits = (r_bin[i0 >> 6] >> sh) ^ (r_bin[nw + (i0 >> 6)] >> sh);
+    const Quad ra0 = load4(r_arith, i0, n), ra1 = load4(r_arith + n, i0, n);
+    Quad b0, b1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const u64 z = ((sb.s[0].v[j] ^ sb.s[1].v[j]) >> 63) ^ ((rbits >> j) & 1ull);
+      b0.v[j] = ra0.v[j] - 2ull * z * ra0.v[j] + z;
+      b1.v[j] = ra1.v[j] - 2ull * z * ra1.v[j];
+    }
+    store4(Out, i0, n, b0);
+    store4(Out + n, i0, n, b1);
+  }
+}
+
 // ---- fused dealer, one element per thread ------------------------------------------------
 // Lanes 4q..4q+3 hold four consecutive elements, i.e. one Philox block of every
 // stream.  For a group of four streams each lane computes the block of one
@@ -494,6 +524,37 @@ __global__ void __launch_bounds__(128) relu_tree_kernel(i64 n, const u64* X, u64
 }
 
 template <int P>
+__global__ void __launch_bounds__(128) ltz_tree_kernel(i64 n, const u64* X, u64* Out,
+                                                       const u64* __restrict__ T,
+                                                       const u64* __restrict__ r_arith,
+                                                       const u64* __restrict__ r_bin, u64 seed,
+                                                       u64 op_id) {
+  const i64 nw = ceil_div(n, 64);
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
+       i += (i64)gridDim.x * blockDim.x) {
+    Shares<P> x;
+#pragma unroll
+    for (int p = 0; p < P; ++p) x.v[p] = X[(i64)p * n + i];
+    const Shares<P> sb = a2b_tree<P>(x, T, n, i, seed, op_id);
+    u64 z = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      z ^= (sb.v[p] >> 63) ^ ((r_bin[(i64)p * nw + (i >> 6)] >> (i & 63)) & 1ull);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const u64 ra = r_arith[(i64)p * n + i];
+      Out[(i64)p * n + i] = ra - 2ull * z * ra + (p == 0 ? z : 0ull);
+    }
+  }
+}
+
+template <int P>
+void launch_ltz_tree(i64 n, const u64* X, u64* Out, const u64* T, const u64* ra, const u64* rb,
+                     u64 seed, u64 op, cudaStream_t s) {
+  ltz_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, Out, T, ra, rb, seed, op);
+}
+
+template <int P>
 void launch_a2b_tree(i64 n, const u64* X, u64* B, const u64* T, u64 seed, u64 op, cudaStream_t s) {
   a2b_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, B, T, seed, op);
 }
@@ -618,6 +679,31 @@ int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uin
     stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,
               (uint64_t)MPC_KS_GATES * n, (uint64_t)MPC_KS_GATES * 6ull * n + 2ull * n + 6ull * n,
               0);
+  return rc;
+}
+
+int mpc_ltz(int P, int64_t n, const uint64_t* X, uint64_t* out, const uint64_t* and_triples,
+            const uint64_t* r_arith, const uint64_t* r_bin, uint64_t seed, uint64_t op_id,
+            void* stream) {
+  if (P == 1) return fail(MPC_EUNSUPPORTED, "comparison needs at least two parties");
+  MPC_CHECK_PARTIES(P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(X && out && and_triples && r_arith && r_bin, "null pointer");
+  cudaStream_t s = as_stream(stream);
+  if (P == 2) {
+    ltz_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(
+        n, (const u64*)X, (u64*)out, (const u64*)and_triples, (const u64*)r_arith,
+        (const u64*)r_bin, seed, op_id);
+  } else {
+    MPC_DISPATCH_P3(P, launch_ltz_tree, n, (const u64*)X, (u64*)out, (const u64*)and_triples,
+                    (const u64*)r_arith, (const u64*)r_bin, seed, op_id, s);
+  }
+  int rc = check_launch("ltz");
+  if (rc == MPC_OK)
+    stats_add(a2b_rounds(P) + 1, (uint64_t)MPC_KS_GATES * (P - 1) * 16ull * n + ceil_div(n, 8),
+              (uint64_t)MPC_KS_GATES * (P - 1) * n,
+              (uint64_t)MPC_KS_GATES * (P - 1) * 3ull * P * n + 2ull * P * n, 0);
   return rc;
 }
 

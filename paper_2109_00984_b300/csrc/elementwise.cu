@@ -271,6 +271,87 @@ __global__ void __launch_bounds__(kThreads) truncate_kernel(i64 total, u64* __re
   }
 }
 
+// ---- Beaver square (App. D.1.1 "Square") and the public affine map --------------------
+// Dealer pair: A[p] = TRIPLE_A(p), b = a^2 shared with TRIPLE_C words + correction.
+__global__ void __launch_bounds__(kThreads) square_pair_kernel(int P, i64 n, u64 seed, u64 op_id,
+                                                               u64* __restrict__ A,
+                                                               u64* __restrict__ B) {
+  const i64 nblk = ceil_div(n, 4);
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
+       t += (i64)gridDim.x * blockDim.x) {
+    const i64 i0 = 4 * t;
+    Quad a = {{0, 0, 0, 0}}, cs = {{0, 0, 0, 0}};
+    for (int p = 0; p < P; ++p) {
+      const Quad ap = as_quad(prg_block(seed, op_id, stream_word2(MPC_ROLE_TRIPLE_A, 0, p), t));
+      store4(A + (i64)p * n, i0, n, ap);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a.v[j] += ap.v[j];
+    }
+    for (int p = 0; p < P - 1; ++p) {
+      const Quad bp = as_quad(prg_block(seed, op_id, stream_word2(MPC_ROLE_TRIPLE_C, 0, p), t));
+      store4(B + (i64)p * n, i0, n, bp);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cs.v[j] += bp.v[j];
+    }
+    Quad last;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) last.v[j] = a.v[j] * a.v[j] - cs.v[j];
+    store4(B + (i64)(P - 1) * n, i0, n, last);
+  }
+}
+
+// Z_p = B_p + 2 eps A_p (+ eps^2 on party 0), eps = sum_p (X_p - A_p) opened in registers.
+template <int P>
+__global__ void __launch_bounds__(kThreads) beaver_square_kernel(i64 n, const u64* X,
+                                                                 const u64* __restrict__ A,
+                                                                 const u64* __restrict__ B,
+                                                                 u64* Z, int trunc_bits) {
+  const i64 nblk = ceil_div(n, 4);
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
+       t += (i64)gridDim.x * blockDim.x) {
+    const i64 i0 = 4 * t;
+    Quad a[P];
+    Quad e = {{0, 0, 0, 0}};
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const Quad x = load4(X + (i64)p * n, i0, n);
+      a[p] = load4(A + (i64)p * n, i0, n);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e.v[j] += x.v[j] - a[p].v[j];
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      Quad z = load4(B + (i64)p * n, i0, n);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        z.v[j] += 2ull * e.v[j] * a[p].v[j];
+        if (p == 0) z.v[j] += e.v[j] * e.v[j];
+        if (trunc_bits > 0) z.v[j] = sar(z.v[j], trunc_bits);
+      }
+      store4(Z + (i64)p * n, i0, n, z);
+    }
+  }
+}
+
+template <int P>
+void launch_beaver_square(i64 n, const u64* X, const u64* A, const u64* B, u64* Z, int trunc_bits,
+                          cudaStream_t s) {
+  beaver_square_kernel<P><<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(n, X, A, B, Z,
+                                                                                 trunc_bits);
+}
+
+// Z_p = scale X_p (+ offset on party 0), then optionally s(Z_p) >> trunc_bits.
+__global__ void __launch_bounds__(kThreads) affine_kernel(int P, i64 n, const u64* X, u64* Z,
+                                                          u64 scale, u64 offset, int trunc_bits) {
+  const i64 total = (i64)P * n;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
+       i += (i64)gridDim.x * blockDim.x) {
+    u64 v = X[i] * scale + (i < n ? offset : 0ull);
+    if (trunc_bits > 0) v = sar(v, trunc_bits);
+    Z[i] = v;
+  }
+}
+
 }  // namespace
 
 }  // namespace mpc
@@ -387,6 +468,43 @@ int mpc_truncate(int P, int64_t n, uint64_t* shares, int frac_bits, int64_t divi
   int rc = check_launch("truncate");
   if (rc == MPC_OK) stats_add(0, 0, 0, 0, 0);
   return rc;
+}
+
+int mpc_ttp_square_pair(int P, int64_t n, uint64_t seed, uint64_t op_id, uint64_t* A, uint64_t* B,
+                        void* stream) {
+  MPC_CHECK_PARTIES(P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(A && B, "null pointer");
+  square_pair_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, as_stream(stream)>>>(
+      P, n, seed, op_id, (u64*)A, (u64*)B);
+  return check_launch("ttp_square_pair");
+}
+
+int mpc_beaver_square(int P, int64_t n, const uint64_t* X, const uint64_t* A, const uint64_t* B,
+                      uint64_t* Z, int trunc_bits, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(X && A && B && Z, "null pointer");
+  MPC_DISPATCH_P(P, launch_beaver_square, n, (const u64*)X, (const u64*)A, (const u64*)B, (u64*)Z,
+                 trunc_bits, as_stream(stream));
+  int rc = check_launch("beaver_square");
+  if (rc == MPC_OK) stats_add(1, 8ull * (uint64_t)n, 0, 2ull * P * (uint64_t)n, 0);
+  return rc;
+}
+
+int mpc_affine(int P, int64_t n, const uint64_t* X, uint64_t* Z, int64_t scale, uint64_t offset,
+               int trunc_bits, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(X && Z, "null pointer");
+  affine_kernel<<<grid_for((i64)P * n, kThreads), kThreads, 0, as_stream(stream)>>>(
+      P, n, (const u64*)X, (u64*)Z, (u64)scale, (u64)offset, trunc_bits);
+  return check_launch("affine");
 }
 
 }  // extern "C"

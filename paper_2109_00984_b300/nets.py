@@ -12,6 +12,12 @@ The weights are shared once by party 1 at construction; the input is shared by
 party 0 in every forward, and the output is revealed at the end (§5.1, §5.2).
 All buffers are allocated up front so that a forward can be captured in a
 CUDA graph.
+
+The dealer's work depends only on shapes and op ids, never on the data, so
+with overlap_dealer (the default) every layer's convolution triple is dealt on
+a second stream that runs ahead of the online phase; the online convolution of
+layer l waits on an event recorded after layer l's triple.  Each stream has its
+own workspace.
 """
 import torch
 
@@ -20,9 +26,10 @@ from . import api
 
 class PrivateConv1dStack:
     def __init__(self, weights, strides, pads, frames, batch=1, algo=api.PLAIN, frac_bits=16,
-                 weight_ops=None, seed=1, device="cuda", fused_relu=True):
+                 weight_ops=None, seed=1, device="cuda", fused_relu=True, overlap_dealer=True):
         self.P = 2
         self.fused_relu = fused_relu
+        self.overlap_dealer = overlap_dealer
         self.algo = algo
         self.frac_bits = frac_bits
         self.seed = seed
@@ -67,18 +74,35 @@ class PrivateConv1dStack:
                          MT=torch.empty((3, P, n), dtype=torch.int64, device=dev))
             self.bufs.append(b)
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        self.dealer_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        self.dealer_stream = torch.cuda.Stream(device=dev) if self.overlap_dealer else None
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
                                     dtype=torch.float64, device=dev)
 
     def forward(self, x, schedule):
         """x: float64 CUDA tensor of the input shape. Returns output shares [P, ...]."""
         seed = schedule["seed"]
+        main = torch.cuda.current_stream()
+        ready = []
+        if self.overlap_dealer:
+            ds = self.dealer_stream
+            ds.wait_stream(main)
+            with torch.cuda.stream(ds):
+                for l, (d, b) in enumerate(zip(self.descs, self.bufs)):
+                    api.ttp_conv2d_triple(self.P, d, seed, schedule["layers"][l]["conv"], self.algo,
+                                          out=(b["A"], b["B"], b["C"]), ws=self.dealer_ws)
+                    ev = torch.cuda.Event()
+                    ev.record(ds)
+                    ready.append(ev)
         api.ring_share(x, self.P, 0, seed, schedule["input_op"], self.frac_bits, out=self.X0)
         X = self.X0
         for l, (d, b) in enumerate(zip(self.descs, self.bufs)):
             ops = schedule["layers"][l]
-            api.ttp_conv2d_triple(self.P, d, seed, ops["conv"], self.algo, out=(b["A"], b["B"], b["C"]),
-                                  ws=self.ws)
+            if self.overlap_dealer:
+                main.wait_event(ready[l])
+            else:
+                api.ttp_conv2d_triple(self.P, d, seed, ops["conv"], self.algo,
+                                      out=(b["A"], b["B"], b["C"]), ws=self.ws)
             api.beaver_conv2d(X, self.W[l], b["A"], b["B"], b["C"], d, self.algo,
                               trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)
             n = b["n"]

@@ -14,6 +14,10 @@ Material op_ids follow the schedule: a layer op with id `op` uses op (triple /
 AND triples), op+1 (B2A bits), op+2 (ReLU's elementwise triple), op+3 (A2B
 masks).  With fused_relu (the default) each ReLU is one private_relu_fused
 call regenerating that material in registers (bit-identical results).
+With overlap_dealer (the default) all convolution / linear triples of a forward
+are dealt first on a second stream, which runs ahead of the online phase (the
+dealer depends on shapes and op ids only); each online product waits on the
+event recorded after its triple.
 """
 import torch
 
@@ -22,9 +26,12 @@ from . import api
 
 class PrivateResNet18:
     def __init__(self, weights, layers, schedule, algo=api.AUTO, frac_bits=16, device="cuda",
-                 fused_relu=True):
+                 fused_relu=True, overlap_dealer=True):
         self.P = 2
         self.fused_relu = fused_relu
+        self.overlap_dealer = overlap_dealer
+        self.dealer_stream = torch.cuda.Stream(device=device) if overlap_dealer else None
+        self.dealer_ws = torch.empty(1, dtype=torch.uint8, device=device)
         self.layers = layers
         self.algo = algo
         self.frac_bits = frac_bits
@@ -36,20 +43,84 @@ class PrivateResNet18:
             self.W[name] = api.ring_share(wt, self.P, 1, self.seed, schedule["weight_base"] + i,
                                           frac_bits)
         self.ws = torch.empty(1, dtype=torch.uint8, device=device)
+        self._triples = {}
 
     def _ws(self, nbytes):
         if self.ws.numel() < nbytes:
             self.ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
         return self.ws
 
+    def _dealer_ws(self, nbytes):
+        if self.dealer_ws.numel() < nbytes:
+            self.dealer_ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self.dealer_ws
+
+    # ---- dealer: convolution / linear triples ---------------------------------------
+    def _deal_conv(self, d, op, ws):
+        return api.ttp_conv2d_triple(self.P, d, self.seed, op, self.algo, device=self.device, ws=ws)
+
+    def _deal_all(self, x_shape, schedule):
+        """Walk the network's shapes and deal every conv / FC triple in order."""
+        ops = schedule["ops"]
+        triples = {}
+        N, _, H, W = x_shape
+        C = 3
+
+        def conv(name, cin, cout, k, stride, pad, h, w, key):
+            d = api.conv_desc(N, cin, h, w, cout, k, k, stride, stride, pad, pad)
+            ws = self._dealer_ws(api.conv2d_triple_workspace_size(self.P, d, self.algo))
+            triples[key] = self._deal_conv(d, ops[key], ws)
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream())
+            triples[key + "#ev"] = ev
+            return api.conv_out_hw(d)
+
+        for layer in self.layers:
+            kind, name = layer[0], layer[1]
+            if kind == "conv":
+                H, W = conv(name, layer[2], layer[3], layer[4], layer[5], layer[6], H, W, name)
+                C = layer[3]
+            elif kind == "maxpool":
+                H = (H + 2 * layer[4] - layer[2]) // layer[3] + 1
+                W = (W + 2 * layer[4] - layer[2]) // layer[3] + 1
+            elif kind == "block":
+                _, name, cin, cout, s = layer
+                h1, w1 = conv(name, cin, cout, 3, s, 1, H, W, name + ".conv1")
+                conv(name, cout, cout, 3, 1, 1, h1, w1, name + ".conv2")
+                if s != 1 or cin != cout:
+                    conv(name, cin, cout, 1, s, 0, H, W, name + ".down")
+                H, W, C = h1, w1, cout
+            elif kind == "fc":
+                cin, cout = layer[2], layer[3]
+                triples[name] = api.ttp_matmul_triple(self.P, N, cout, cin, self.seed, ops[name],
+                                                      self.algo, device=self.device)
+                ev = torch.cuda.Event()
+                ev.record(torch.cuda.current_stream())
+                triples[name + "#ev"] = ev
+        return triples
+
+    def _triple(self, key):
+        t = self._triples.get(key)
+        if t is None:
+            return None
+        main = torch.cuda.current_stream()
+        main.wait_event(self._triples[key + "#ev"])
+        for tensor in t:        # allocated on the dealer stream, consumed here
+            tensor.record_stream(main)
+        return t
+
     # ---- layer operations ---------------------------------------------------------
-    def conv(self, X, Wsh, stride, pad, op):
+    def conv(self, X, Wsh, stride, pad, op, key=None):
         P, N, Cin, H, W = X.shape
         Cout, _, k, _ = Wsh.shape[1:]
         d = api.conv_desc(N, Cin, H, W, Cout, k, k, stride, stride, pad, pad)
-        ws = self._ws(max(api.conv2d_workspace_size(P, d, self.algo),
-                          api.conv2d_triple_workspace_size(P, d, self.algo)))
-        A, B, C = api.ttp_conv2d_triple(P, d, self.seed, op, self.algo, device=self.device, ws=ws)
+        trip = self._triple(key) if key is not None else None
+        if trip is None:
+            ws = self._ws(max(api.conv2d_workspace_size(P, d, self.algo),
+                              api.conv2d_triple_workspace_size(P, d, self.algo)))
+            trip = self._deal_conv(d, op, ws)
+        A, B, C = trip
+        ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d(X, Wsh, A, B, C, d, self.algo, self.frac_bits, ws=ws)
 
     def relu(self, X, op):
@@ -84,22 +155,31 @@ class PrivateResNet18:
             level += 1
         return vals[0].reshape(shape)
 
-    def fc(self, X, Wsh, op):
+    def fc(self, X, Wsh, op, key=None):
         P, N, Cin = X.shape
         Cout = Wsh.shape[2]
-        A, B, C = api.ttp_matmul_triple(P, N, Cout, Cin, self.seed, op, self.algo,
-                                        device=self.device)
+        trip = self._triple(key) if key is not None else None
+        if trip is None:
+            trip = api.ttp_matmul_triple(P, N, Cout, Cin, self.seed, op, self.algo,
+                                         device=self.device)
+        A, B, C = trip
         return api.beaver_matmul(X, Wsh, A, B, C, self.algo, self.frac_bits)
 
     # ---- forward ----------------------------------------------------------------------
     def forward(self, x, schedule):
         """x: float64 CUDA images (N, 3, H, W).  Returns logit shares [2, N, classes]."""
         ops = schedule["ops"]
+        self._triples = {}
+        if self.overlap_dealer:
+            ds = self.dealer_stream
+            ds.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(ds):
+                self._triples = self._deal_all(tuple(x.shape), schedule)
         X = api.ring_share(x, self.P, 0, self.seed, ops["input"], self.frac_bits)
         for layer in self.layers:
             kind, name = layer[0], layer[1]
             if kind == "conv":
-                X = self.conv(X, self.W[name], layer[5], layer[6], ops[name])
+                X = self.conv(X, self.W[name], layer[5], layer[6], ops[name], name)
             elif kind == "relu":
                 X = self.relu(X, ops[name])
             elif kind == "maxpool":
@@ -107,18 +187,20 @@ class PrivateResNet18:
                                  [ops[f"{name}.{l}"] for l in range(4)])
             elif kind == "block":
                 _, name, cin, cout, s = layer
-                Y = self.conv(X, self.W[name + ".conv1"], s, 1, ops[name + ".conv1"])
+                Y = self.conv(X, self.W[name + ".conv1"], s, 1, ops[name + ".conv1"], name + ".conv1")
                 Y = self.relu(Y, ops[name + ".relu1"])
-                Y = self.conv(Y, self.W[name + ".conv2"], 1, 1, ops[name + ".conv2"])
+                Y = self.conv(Y, self.W[name + ".conv2"], 1, 1, ops[name + ".conv2"], name + ".conv2")
                 if s != 1 or cin != cout:
-                    S = self.conv(X, self.W[name + ".down"], s, 0, ops[name + ".down"])
+                    S = self.conv(X, self.W[name + ".down"], s, 0, ops[name + ".down"],
+                                  name + ".down")
                 else:
                     S = X
                 X = self.relu(api.add(Y, S), ops[name + ".relu2"])
             elif kind == "avgpool":
                 X = api.global_avgpool(X)
             elif kind == "fc":
-                X = self.fc(X, self.W[name], ops[name])
+                X = self.fc(X, self.W[name], ops[name], name)
+        self._triples = {}
         return X
 
     def reveal(self, shares):

@@ -359,3 +359,43 @@ def test_private_relu_fused_dealer(mpc, n, rng):
     ref = binary.private_relu(X, T, ra, rb, mt, SEED, op + 3)
     got = host(mpc.private_relu_fused(dev(X), SEED, op))
     assert np.array_equal(got, ref)
+
+
+# ---- square, affine, comparators, multiplexing ----------------------------------------
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_beaver_square(mpc, P, rng):
+    n = 5001
+    X = u64(rng, (P, n))
+    A, B = mpc.ttp_square_pair(P, n, SEED, 301)
+    oA, oB = dealer.square_pair(P, n, SEED, 301)
+    assert np.array_equal(host(A), oA) and np.array_equal(host(B), oB)
+    got = host(mpc.beaver_square(dev(X), A, B, trunc_bits=16))
+    assert np.array_equal(got, truncation.truncate(beaver.beaver_square(X, oA, oB), 16))
+
+
+def test_affine(mpc, rng):
+    X = u64(rng, (3, 777))
+    got = host(mpc.affine(dev(X), -7, 99, trunc_bits=3))
+    assert np.array_equal(got, beaver.affine(X, -7, 99, trunc_bits=3))
+
+
+@pytest.mark.parametrize("P", [2, 3])
+def test_comparators(mpc, P, rng):
+    from oracle import compare
+    a = rng.integers(-50, 50, 600) * 65536
+    b = rng.integers(-50, 50, 600) * 65536
+    b[:150] = a[:150]
+    X = sharing.share(a.astype(np.int64).view(np.uint64), P, 0, SEED, 5)
+    Y = sharing.share(b.astype(np.int64).view(np.uint64), P, P - 1, SEED, 6)
+    for name in ("lt", "gt", "ge", "le", "eq", "ne"):
+        got = host(getattr(mpc, name)(dev(X), dev(Y), SEED, 3000))
+        assert np.array_equal(got, getattr(compare, name)(X, Y, SEED, 3000)), name
+
+
+def test_mux(mpc, rng):
+    from oracle import compare
+    c = rng.integers(0, 2, 900).astype(np.int64)
+    Cs = sharing.share(c.view(np.uint64), 2, 0, SEED, 9)
+    X, Y = u64(rng, (2, 900)), u64(rng, (2, 900))
+    got = host(mpc.mux(dev(Cs), dev(X), dev(Y), SEED, 4000))
+    assert np.array_equal(got, compare.mux(Cs, X, Y, SEED, 4000))
