@@ -416,6 +416,87 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
 int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
                            uint64_t op_id, void* stream);
 
+/* ---- function approximations (App. D.2), two parties, fused dealer -------- */
+/* Each call below evaluates one function elementwise on two-party shares of
+ * fixed-point values (2^16) in ONE launch per element range: every dealer
+ * word is regenerated from Philox in registers and every opening is a sum of
+ * the two shares, so HBM traffic is X and Y only.  Step k of a function (a
+ * Beaver product, a square, a comparison) draws its material at op id
+ * op_id + 10 k, in the order the steps run.  X, Y: device u64 [2][n]; Y may
+ * alias X (except for mpc_softmax).  P must be 2 (MPC_EUNSUPPORTED otherwise).
+ * Products of two scaled values are followed by the two-party truncation by
+ * 16 bits, so results carry a few ulps (2^-16) of error beyond the method's. */
+#define MPC_APPROX_MAX_EXP_ITERS 20
+#define MPC_APPROX_MAX_NR_ITERS 64
+
+/* exp(x) by the limit approximation (1 + x / 2^iters)^(2^iters) (App. D.2.1):
+ * a truncation by `iters` bits, then `iters` Beaver squarings (iters in
+ * 1..20; 8 is the paper's default).  Accurate for x <~ 2^iters / 10; for
+ * x < -2^iters the base turns negative. */
+int mpc_exp(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+            int iters, void* stream);
+
+/* 1/x by Newton-Raphson y <- y (2 - x y) (App. D.2.2), nr_iters iterations
+ * from y0 = 3 exp(0.5 - x) + 0.003 (exp with exp_iters).  With all_positive
+ * the input must be > 0; otherwise 1/x = sgn(x) / |x| with one comparison and
+ * two more products.  Converges for 0 < x y0 < 2 (x up to ~ 200 by default). */
+int mpc_reciprocal(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
+                   uint64_t op_id, int all_positive, int exp_iters, int nr_iters, void* stream);
+
+/* sigmoid(x) (App. D.2.5): [x < 0] and |x| from one comparison and one product,
+ * sigma(|x|) = 1 / (1 + exp(-|x|)) by Newton-Raphson from 0.75, then the
+ * multiplexing product [x < 0] ? 1 - sigma(|x|) : sigma(|x|). */
+int mpc_sigmoid(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+                int exp_iters, int nr_iters, void* stream);
+
+/* tanh(x) = 2 sigmoid(2x) - 1 (App. D.2.5). */
+int mpc_tanh(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+             int exp_iters, int nr_iters, void* stream);
+
+/* erf(x) by the Maclaurin series 2/sqrt(pi) sum_{k=0}^{terms} (-1)^k
+ * x^(2k+1) / (k! (2k+1)) (App. D.2.6; terms = 8 by default, at most 16):
+ * one square, then `terms` products; poor for |x| > 1 as the paper notes. */
+int mpc_erf(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+            int terms, void* stream);
+
+/* x^(-1/2) for x > 0 by y <- y (3 - x y^2) / 2 (App. D.2.3), nr_iters
+ * iterations from y0 = 3 g^16 + 0.3 g + 0.05 with g = exp(-x / 16) (the paper
+ * gives no initial value; this one converges on [0.01, 100]).  mpc_sqrt
+ * multiplies the result by x. */
+int mpc_inv_sqrt(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
+                 uint64_t op_id, int exp_iters, int nr_iters, void* stream);
+int mpc_sqrt(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+             int exp_iters, int nr_iters, void* stream);
+
+/* ln(x) for x > 0 by Householder iterations (App. D.2.4): h = 1 - x exp(-y),
+ * y <- y - sum_{k=1}^{order} h^k / k, `iters` iterations (default 3, order 8)
+ * from y0 = x / 120 - 20 exp(-2x - 1) + 3.  With the limit approximation
+ * inside, the iteration converges to 256 (1 - x^(-1/256)). */
+int mpc_log(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed, uint64_t op_id,
+            int exp_iters, int iters, int order, void* stream);
+
+/* Maximum over the last axis (Table "max"/"argmax": tree reduction): X shares
+ * [2][rows][m] -> out [2][rows].  Level l pairs adjacent elements,
+ * max(a, b) = b + ReLU(a - b) with the ReLU of all pairs of the level at op id
+ * op_id + 10 l (material indexed by the flat pair index row * floor(m'/2) + i);
+ * an odd last element moves up unchanged.  Exact (no truncation).  workspace:
+ * device, at least mpc_max_workspace_size bytes (none needed for m == 1). */
+size_t mpc_max_workspace_size(int P, int64_t rows, int64_t m);
+int mpc_max_lastdim(int P, int64_t rows, int64_t m, const uint64_t* X, uint64_t* out,
+                    void* workspace, size_t ws_bytes, uint64_t seed, uint64_t op_id,
+                    void* stream);
+
+/* Softmax over the last axis (App. D.2, Table "softmax"): the max tree as in
+ * mpc_max_lastdim, e = exp(x - max) with the next exp_iters op ids, s = sum of
+ * e over the row (local), r = reciprocal(s) (positive form, s >= 1), then
+ * Y = e * r with the elementwise triple at the next op id (flat index).
+ * X, Y: device u64 [2][rows][m], Y must not alias X.  workspace: device, at
+ * least mpc_softmax_workspace_size bytes.  Four to ceil(log2 m) + 4 launches. */
+size_t mpc_softmax_workspace_size(int P, int64_t rows, int64_t m);
+int mpc_softmax(int P, int64_t rows, int64_t m, const uint64_t* X, uint64_t* Y, void* workspace,
+                size_t ws_bytes, uint64_t seed, uint64_t op_id, int exp_iters, int nr_iters,
+                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

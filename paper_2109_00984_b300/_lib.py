@@ -79,6 +79,20 @@ SIGNATURES = {
     "mpc_ltz": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64, c_vp]),
     "mpc_affine": (c_int, [c_int, c_i64, c_vp, c_vp, c_i64, c_u64, c_int, c_vp]),
     "mpc_private_relu_fused": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_vp]),
+    "mpc_exp": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_vp]),
+    "mpc_reciprocal": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_int, c_vp]),
+    "mpc_sigmoid": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_vp]),
+    "mpc_tanh": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_vp]),
+    "mpc_erf": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_vp]),
+    "mpc_inv_sqrt": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_vp]),
+    "mpc_sqrt": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_vp]),
+    "mpc_log": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_int, c_vp]),
+    "mpc_max_workspace_size": (c_size, [c_int, c_i64, c_i64]),
+    "mpc_max_lastdim": (c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_size, c_u64, c_u64,
+                                c_vp]),
+    "mpc_softmax_workspace_size": (c_size, [c_int, c_i64, c_i64]),
+    "mpc_softmax": (c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_size, c_u64, c_u64, c_int,
+                            c_int, c_vp]),
     "mpc_truncate_nparty": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_int, c_vp]),
     "mpc_ttp_trunc_pairs": (c_int, [c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
     "mpc_add": (c_int, [c_int, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp]),

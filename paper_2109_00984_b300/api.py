@@ -492,3 +492,80 @@ def mux(C, X, Y, seed, op_id):
     A, B, T = ttp_mul_triple(P, n, seed, op_id, device=C.device)
     prod = beaver_mul(C, sub(X, Y), A.view(C.shape), B.view(C.shape), T.view(C.shape))
     return add(prod, Y)
+
+
+# ---- function approximations (App. D.2), two parties, one fused launch each ----------
+# Step k of a function draws its dealer material at op id op_id + 10 k.
+EXP_ITERS = 8
+NR_ITERS = 10
+ERF_TERMS = 8
+LOG_ITERS = 3
+LOG_ORDER = 8
+
+
+def _elementwise(fn, X, out, *args):
+    P = X.shape[0]
+    n = X.numel() // P
+    out = torch.empty_like(X) if out is None else out
+    _check(fn(P, n, _ptr(X), _ptr(out), *args, _stream()))
+    return out
+
+
+def exp(X, seed, op_id, iters=EXP_ITERS, out=None):
+    """exp by the limit approximation (1 + x / 2^iters)^(2^iters)."""
+    return _elementwise(_L().mpc_exp, X, out, seed, op_id, iters)
+
+
+def reciprocal(X, seed, op_id, all_positive=False, exp_iters=EXP_ITERS, nr_iters=NR_ITERS,
+               out=None):
+    """1/x by Newton-Raphson from 3 exp(0.5 - x) + 0.003; sgn(x) / |x| unless all_positive."""
+    return _elementwise(_L().mpc_reciprocal, X, out, seed, op_id, int(bool(all_positive)),
+                        exp_iters, nr_iters)
+
+
+def sigmoid(X, seed, op_id, exp_iters=EXP_ITERS, nr_iters=NR_ITERS, out=None):
+    return _elementwise(_L().mpc_sigmoid, X, out, seed, op_id, exp_iters, nr_iters)
+
+
+def tanh(X, seed, op_id, exp_iters=EXP_ITERS, nr_iters=NR_ITERS, out=None):
+    return _elementwise(_L().mpc_tanh, X, out, seed, op_id, exp_iters, nr_iters)
+
+
+def erf(X, seed, op_id, terms=ERF_TERMS, out=None):
+    return _elementwise(_L().mpc_erf, X, out, seed, op_id, terms)
+
+
+def inv_sqrt(X, seed, op_id, exp_iters=EXP_ITERS, nr_iters=NR_ITERS, out=None):
+    return _elementwise(_L().mpc_inv_sqrt, X, out, seed, op_id, exp_iters, nr_iters)
+
+
+def sqrt(X, seed, op_id, exp_iters=EXP_ITERS, nr_iters=NR_ITERS, out=None):
+    return _elementwise(_L().mpc_sqrt, X, out, seed, op_id, exp_iters, nr_iters)
+
+
+def log(X, seed, op_id, exp_iters=EXP_ITERS, iters=LOG_ITERS, order=LOG_ORDER, out=None):
+    return _elementwise(_L().mpc_log, X, out, seed, op_id, exp_iters, iters, order)
+
+
+def max_lastdim(X, seed, op_id, out=None, ws=None):
+    """Maximum over the last axis of shares [2, ..., m] -> [2, ...] (exact, ReLU tree)."""
+    P, m = X.shape[0], X.shape[-1]
+    rows = X.numel() // (P * m)
+    out = torch.empty(X.shape[:-1], dtype=torch.int64, device=X.device) if out is None else out
+    need = _L().mpc_max_workspace_size(P, rows, m)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_max_lastdim(P, rows, m, _ptr(X), _ptr(out), _ptr(ws, "ws", torch.uint8),
+                                ws.numel(), seed, op_id, _stream()))
+    return out
+
+
+def softmax(X, seed, op_id, exp_iters=EXP_ITERS, nr_iters=NR_ITERS, out=None, ws=None):
+    """Softmax over the last axis of shares [2, ..., m]."""
+    P, m = X.shape[0], X.shape[-1]
+    rows = X.numel() // (P * m)
+    out = torch.empty_like(X) if out is None else out
+    need = _L().mpc_softmax_workspace_size(P, rows, m)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_softmax(P, rows, m, _ptr(X), _ptr(out), _ptr(ws, "ws", torch.uint8), ws.numel(),
+                            seed, op_id, exp_iters, nr_iters, _stream()))
+    return out

@@ -6,6 +6,7 @@
 // Philox block of each binary zero-share stream.
 #include "common.cuh"
 #include "host.hpp"
+#include "fused.cuh"
 
 namespace mpc {
 
@@ -259,122 +260,19 @@ __global__ void __launch_bounds__(kThreads) ltz_kernel(i64 n, const u64* X, u64*
   }
 }
 
-// ---- fused dealer, one element per thread ------------------------------------------------
-// Lanes 4q..4q+3 hold four consecutive elements, i.e. one Philox block of every
-// stream.  For a group of four streams each lane computes the block of one
-// stream and the words are exchanged by shuffles, so every lane ends with its
-// element's word of all four streams: the same Philox work as one block per
-// four elements, with one element of protocol state per thread.
-struct Quad4 {
-  u64 w[4];  // word of this lane's element in streams 0..3 of the group
-};
-
-__device__ __forceinline__ Quad4 quad_gen(u64 seed, u64 op0, u64 w0, u64 op1, u64 w1, u64 op2,
-                                          u64 w2, u64 op3, u64 w3, i64 blk, int j) {
-  const u64 op = j == 0 ? op0 : j == 1 ? op1 : j == 2 ? op2 : op3;
-  const u64 wd = j == 0 ? w0 : j == 1 ? w1 : j == 2 ? w2 : w3;
-  const u64x4 b = prg_block(seed, op, wd, blk);
-  const int base = (threadIdx.x & 31) & ~3;
-  Quad4 q;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    u64 mine = 0;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const u64 v = __shfl_sync(0xffffffffu, b.v[w], base + s);
-      if (w == j) mine = v;
-    }
-    q.w[s] = mine;
-  }
-  return q;
-}
-
-struct Sh2 {
-  u64 v[2];
-};
-
-__device__ __forceinline__ Sh2 xr2(Sh2 a, Sh2 b) { return Sh2{{a.v[0] ^ b.v[0], a.v[1] ^ b.v[1]}}; }
-__device__ __forceinline__ Sh2 shl2(Sh2 a, int d) { return Sh2{{a.v[0] << d, a.v[1] << d}}; }
-
-// AND with a triple (a0, a1, b0, b1, c0), c1 = ((a0 ^ a1) & (b0 ^ b1)) ^ c0.
-__device__ __forceinline__ Sh2 and2(Sh2 x, Sh2 y, const Quad4& ab, u64 c0) {
-  const u64 a0 = ab.w[0], a1 = ab.w[1], b0 = ab.w[2], b1 = ab.w[3];
-  const u64 c1 = ((a0 ^ a1) & (b0 ^ b1)) ^ c0;
-  const u64 eps = x.v[0] ^ a0 ^ x.v[1] ^ a1;
-  const u64 del = y.v[0] ^ b0 ^ y.v[1] ^ b1;
-  return Sh2{{c0 ^ (eps & b0) ^ (a0 & del) ^ (eps & del), c1 ^ (eps & b1) ^ (a1 & del)}};
-}
-
 __global__ void __launch_bounds__(256) relu_fused_quad_kernel(i64 n, const u64* X, u64* Y,
                                                               u64 seed, u64 op) {
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
   const int j = threadIdx.x & 3;
-  const u64 op_and = op, op_b2a = op + 1, op_mul = op + 2, op_mask = op + 3;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < npad; i += stride) {
     const bool valid = i < n;
     const i64 blk = i >> 2;
     Sh2 x{{valid ? X[i] : 0ull, valid ? X[n + i] : 0ull}};
-    // A2B of -x: binary sharings of both parties' shares (ZERO_BIN masks).
-    const Quad4 m = quad_gen(seed, op_mask, stream_word2(MPC_ROLE_ZERO_BIN, 0, 0), op_mask,
-                             stream_word2(MPC_ROLE_ZERO_BIN, 0, 1), op_mask,
-                             stream_word2(MPC_ROLE_ZERO_BIN, 1, 0), op_mask,
-                             stream_word2(MPC_ROLE_ZERO_BIN, 1, 1), blk, j);
-    const u64 y0 = 0ull - x.v[0], y1 = 0ull - x.v[1];
-    const Sh2 u{{m.w[0] ^ m.w[1] ^ y0, m.w[1] ^ m.w[0]}};
-    const Sh2 v{{m.w[2] ^ m.w[3], m.w[3] ^ m.w[2] ^ y1}};
-    // Kogge-Stone: gate g uses AND_A/B (g, 0/1) and AND_C (g, 0).
-    Quad4 c0s[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      c0s[q] = quad_gen(seed, op_and, stream_word2(MPC_ROLE_AND_C, 4 * q + 0, 0), op_and,
-                        stream_word2(MPC_ROLE_AND_C, 4 * q + 1, 0), op_and,
-                        stream_word2(MPC_ROLE_AND_C, 4 * q + 2, 0), op_and,
-                        stream_word2(MPC_ROLE_AND_C, 4 * q + 3, 0), blk, j);
-    auto gate_ab = [&](int g) {
-      return quad_gen(seed, op_and, stream_word2(MPC_ROLE_AND_A, g, 0), op_and,
-                      stream_word2(MPC_ROLE_AND_A, g, 1), op_and,
-                      stream_word2(MPC_ROLE_AND_B, g, 0), op_and,
-                      stream_word2(MPC_ROLE_AND_B, g, 1), blk, j);
-    };
-    int gate = 0;
-    Sh2 G = and2(u, v, gate_ab(gate), c0s[0].w[0]);
-    ++gate;
-    Sh2 Pp = xr2(u, v);
-    const Sh2 P0 = Pp;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-      const int d = 1 << r;
-      const Sh2 t = and2(Pp, shl2(G, d), gate_ab(gate), c0s[gate >> 2].w[gate & 3]);
-      ++gate;
-      if (d < 32) {
-        Pp = and2(Pp, shl2(Pp, d), gate_ab(gate), c0s[gate >> 2].w[gate & 3]);
-        ++gate;
-      }
-      G = xr2(G, t);
-    }
-    const Sh2 sb = xr2(P0, shl2(G, 1));
-    // B2A pair (r, <r>_0, [r]_0) and the elementwise triple's c_0 share one group.
-    const Quad4 rq = quad_gen(seed, op_b2a, stream_word2(MPC_ROLE_B2A_R, 0, MPC_TTP_PARTY), op_b2a,
-                              stream_word2(MPC_ROLE_B2A_BIN, 0, 0), op_b2a,
-                              stream_word2(MPC_ROLE_B2A_ARITH, 0, 0), op_mul,
-                              stream_word2(MPC_ROLE_TRIPLE_C, 0, 0), blk, j);
-    const u64 rbit = rq.w[0] & 1ull;  // <r>_0 ^ <r>_1 = r
-    const u64 z = ((sb.v[0] ^ sb.v[1]) >> 63) ^ rbit;
-    const u64 ra0 = rq.w[2], ra1 = rbit - rq.w[2];
-    const u64 bit0 = ra0 - 2ull * z * ra0 + z, bit1 = ra1 - 2ull * z * ra1;
-    // Beaver product x * [b] with the elementwise triple (op + 2).
-    const Quad4 t = quad_gen(seed, op_mul, stream_word2(MPC_ROLE_TRIPLE_A, 0, 0), op_mul,
-                             stream_word2(MPC_ROLE_TRIPLE_A, 0, 1), op_mul,
-                             stream_word2(MPC_ROLE_TRIPLE_B, 0, 0), op_mul,
-                             stream_word2(MPC_ROLE_TRIPLE_B, 0, 1), blk, j);
-    const u64 A0 = t.w[0], A1 = t.w[1], B0 = t.w[2], B1 = t.w[3], C0 = rq.w[3];
-    const u64 C1 = (A0 + A1) * (B0 + B1) - C0;
-    const u64 E = (x.v[0] - A0) + (x.v[1] - A1);
-    const u64 F = (bit0 - B0) + (bit1 - B1);
+    const Sh2 y = relu_quad(x, seed, op, blk, j);
     if (valid) {
-      Y[i] = C0 + E * B0 + A0 * F + E * F;
-      Y[n + i] = C1 + E * B1 + A1 * F;
+      Y[i] = y.v[0];
+      Y[n + i] = y.v[1];
     }
   }
 }

@@ -1,0 +1,134 @@
+"""Function approximations (App. D.2) on the GPU against the oracle, bit-exact.
+
+Each fused kernel regenerates the dealer's material in registers; the oracle
+draws it from the dealer functions and runs the steps one by one.  Sizes span
+several thread blocks with a ragged tail (n = 4099 is not a multiple of the
+4-lane Philox quads nor of the 256-thread blocks), and iteration counts that
+are not multiples of the kernels' word-chunk sizes exercise the padding paths.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import dev, host  # noqa: E402
+
+from oracle import approx, fixed, sharing  # noqa: E402
+
+SEED = 0x5EED_A99
+N = 4099
+
+
+@pytest.fixture(scope="module")
+def mpc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_00984_b300 as m
+    return m
+
+
+def _shares(lo, hi, n, seed=11, log=False):
+    rng = np.random.default_rng(seed)
+    if log:
+        v = np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+    else:
+        v = rng.uniform(lo, hi, n)
+    return sharing.share(fixed.encode(v), 2, 0, SEED, 77)
+
+
+@pytest.mark.parametrize("iters", [8, 5, 1])
+@pytest.mark.parametrize("n", [N, 3, 1, 0])
+def test_exp(mpc, iters, n):
+    X = _shares(-6, 3, n)
+    ref = approx.exp(X, SEED, approx.OpIds(1000), iters=iters)
+    got = host(mpc.exp(dev(X), SEED, 1000, iters=iters))
+    assert np.array_equal(got, ref)
+
+
+def test_exp_in_place(mpc):
+    X = _shares(-6, 3, N)
+    d = dev(X)
+    mpc.exp(d, SEED, 1000, out=d)
+    assert np.array_equal(host(d), approx.exp(X, SEED, approx.OpIds(1000)))
+
+
+@pytest.mark.parametrize("nr", [10, 3])
+def test_reciprocal_positive(mpc, nr):
+    X = _shares(0.1, 50, N, log=True)
+    ref = approx.reciprocal_pos(X, SEED, approx.OpIds(2000), iters=nr)
+    got = host(mpc.reciprocal(dev(X), SEED, 2000, all_positive=True, nr_iters=nr))
+    assert np.array_equal(got, ref)
+
+
+def test_reciprocal_signed(mpc):
+    X = _shares(-30, 30, N)
+    ref = approx.reciprocal(X, SEED, approx.OpIds(3000))
+    got = host(mpc.reciprocal(dev(X), SEED, 3000))
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("nr", [10, 1])
+def test_sigmoid(mpc, nr):
+    X = _shares(-12, 12, N)
+    ref = approx.sigmoid(X, SEED, approx.OpIds(4000), iters=nr)
+    got = host(mpc.sigmoid(dev(X), SEED, 4000, nr_iters=nr))
+    assert np.array_equal(got, ref)
+
+
+def test_tanh(mpc):
+    X = _shares(-5, 5, N)
+    ref = approx.tanh(X, SEED, approx.OpIds(5000))
+    got = host(mpc.tanh(dev(X), SEED, 5000))
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("terms", [8, 5, 1, 0])
+def test_erf(mpc, terms):
+    X = _shares(-1.5, 1.5, N)
+    ref = approx.erf(X, SEED, approx.OpIds(6000), terms=terms)
+    got = host(mpc.erf(dev(X), SEED, 6000, terms=terms))
+    assert np.array_equal(got, ref)
+
+
+def test_inv_sqrt_and_sqrt(mpc):
+    X = _shares(0.01, 100, N, log=True)
+    ref = approx.inv_sqrt(X, SEED, approx.OpIds(7000))
+    assert np.array_equal(host(mpc.inv_sqrt(dev(X), SEED, 7000)), ref)
+    ref = approx.sqrt(X, SEED, approx.OpIds(8000), iters=7)
+    assert np.array_equal(host(mpc.sqrt(dev(X), SEED, 8000, nr_iters=7)), ref)
+
+
+@pytest.mark.parametrize("iters,order", [(3, 8), (1, 5), (2, 1)])
+def test_log(mpc, iters, order):
+    X = _shares(0.01, 100, N, log=True)
+    ref = approx.log(X, SEED, approx.OpIds(9000), iters=iters, order=order)
+    got = host(mpc.log(dev(X), SEED, 9000, iters=iters, order=order))
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rows,m", [(7, 197), (1000, 13), (5, 2), (4, 3), (3, 1), (0, 5)])
+def test_max_lastdim(mpc, rows, m):
+    rng = np.random.default_rng(rows * 1000 + m)
+    v = rng.integers(-(1 << 40), 1 << 40, (rows, m)).astype(np.int64)
+    X = sharing.share(v.view(np.uint64), 2, 0, SEED, 5)
+    ref = approx.max_lastdim(X, SEED, approx.OpIds(10000)) if rows else np.zeros((2, 0), np.uint64)
+    got = host(mpc.max_lastdim(dev(X), SEED, 10000))
+    assert np.array_equal(got, ref)
+    if rows:
+        assert np.array_equal(sharing.reveal(got).view(np.int64), v.max(axis=-1))
+
+
+@pytest.mark.parametrize("rows,m", [(12, 197), (33, 50), (3, 2), (5, 1)])
+def test_softmax(mpc, rows, m):
+    rng = np.random.default_rng(rows + m)
+    X = sharing.share(fixed.encode(rng.normal(0, 2, (rows, m))), 2, 0, SEED, 6)
+    ref = approx.softmax(X, SEED, approx.OpIds(20000))
+    got = host(mpc.softmax(dev(X), SEED, 20000))
+    assert np.array_equal(got, ref)
+
+
+def test_approx_rejects_other_party_counts(mpc):
+    X = dev(np.zeros((3, 8), np.uint64))
+    with pytest.raises(mpc.MPCError):
+        mpc.exp(X, SEED, 1)
