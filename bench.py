@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["plain", "limb", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="speech", choices=["speech", "gemm", "batched", "resnet"],
+    ap.add_argument("--workload", default="speech",
+                    choices=["speech", "gemm", "batched", "resnet", "approx"],
                     help="speech: the private conv stack (default); gemm: ring GEMM sweep; "
                          "batched: 512 uneven Beaver matmuls")
     ap.add_argument("--sizes", default="1024,2048,4096,8192")
@@ -555,6 +556,105 @@ def run_resnet(args):
     print(json.dumps(line), flush=True)
 
 
+# Philox4x64-10 blocks each fused function regenerates per element (one quad_gen
+# call = one block per element): exp = 2 chunks of 3; a product = 5/4, a square
+# = 3/4; a comparison = 16; see the kernels' word lists.
+APPROX_BLOCKS = {"exp": 6, "reciprocal": 50, "sigmoid": 50, "tanh": 50, "erf": 12,
+                 "inv_sqrt": 49, "log": 54}
+# ALU roofline of a fused-dealer kernel: a Philox4x64-10 block is 10 rounds of two
+# 64x64->128-bit products, each 4 wide 32x32->64 partial products = 8 32-bit
+# multiply results, i.e. 160 per block; 64 such results per clock per SM.
+PHILOX_PEAK_BLOCKS = 64 * 148 * 2032e6 / 160
+
+
+def run_approx(args):
+    """Fused function approximations (two parties) on 2^25 elements each, and the
+    ViT-B/16 attention softmax (12 layers x 12 heads x 197 rows of 197 per image).
+
+    Inputs (1 GiB of shares per function) exceed L2, so no flush is needed.
+    """
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = 1 << 25
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    domains = {"exp": (-6, 3), "reciprocal": (-30, 30), "sigmoid": (-12, 12), "tanh": (-5, 5),
+               "erf": (-1.5, 1.5), "inv_sqrt": (0.01, 100), "log": (0.01, 100)}
+    calls = {"exp": mpc.exp, "reciprocal": mpc.reciprocal, "sigmoid": mpc.sigmoid,
+             "tanh": mpc.tanh, "erf": mpc.erf, "inv_sqrt": mpc.inv_sqrt, "log": mpc.log}
+    stream = torch.cuda.current_stream()
+    steps = max(1, args.steps)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    funcs = {}
+    for name, (lo, hi) in domains.items():
+        x = torch.rand(n, generator=g, device=dev, dtype=torch.float64) * (hi - lo) + lo
+        X = mpc.ring_share(x, 2, 0, 7, 1)
+        Y = torch.empty_like(X)
+        ms = timed(lambda: calls[name](X, 7, 100, out=Y))
+        rate = n / (ms / 1e3)
+        funcs[name] = {"ms": ms, "elements_per_s": rate,
+                       "philox_blocks_per_s": rate * APPROX_BLOCKS[name],
+                       "alu_frac": rate * APPROX_BLOCKS[name] / PHILOX_PEAK_BLOCKS}
+        del X, Y, x
+    # ViT-B/16 attention softmax, one image: 144 heads x 197 rows of 197 logits
+    rows, m = 12 * 12 * 197, 197
+    logits = torch.randn(rows, m, generator=g, device=dev, dtype=torch.float64) * 2
+    S = mpc.ring_share(logits, 2, 0, 7, 2)
+    Ys = torch.empty_like(S)
+    ws = torch.empty(mpc._lib.load().mpc_softmax_workspace_size(2, rows, m), dtype=torch.uint8,
+                     device=dev)
+    mpc.reset_stats()
+    sm_ms = timed(lambda: mpc.softmax(S, 7, 100, out=Ys, ws=ws))
+    stats = mpc.get_stats()
+    clk = clocks.stop()
+    # blocks per logit: the max tree's ReLUs (17 per pair, m - 1 pairs per row), exp (6),
+    # the final product (2), the reciprocal per row (31)
+    sm_blocks = rows * (17 * (m - 1) + 6 * m + 2 * m + 31)
+    head = funcs["sigmoid"]
+    line = {"metric": "fused private sigmoid throughput (2 parties, Z/2^64, 2^16 fixed point)",
+            "value": head["elements_per_s"], "unit": "elements/s", "higher_is_better": True,
+            "steps": steps, "warmup": max(3, args.warmup), "dtype": "u64",
+            "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "function approximations, 2^25 elements each, inputs > L2 "
+                                   "(no flush); ViT-B/16 softmax 28368 rows x 197",
+                       "exp_iters": 8, "nr_iters": 10, "erf_terms": 8, "log_iters": 3,
+                       "log_order": 8},
+            "roofline": {"bound": "alu", "achieved": head["philox_blocks_per_s"] / 1e9,
+                         "peak": PHILOX_PEAK_BLOCKS / 1e9, "unit": "G Philox blocks/s",
+                         "frac": head["alu_frac"], "traffic": None,
+                         "peak_source": "derived: 64 32-bit multiply results/clk/SM, 148 SMs, "
+                                        "2032 MHz, 160 per Philox4x64-10 block"},
+            "functions": funcs,
+            "vit_softmax": {"ms_per_image": sm_ms, "images_per_s": 1e3 / sm_ms,
+                            "rows": rows, "m": m,
+                            "philox_blocks_per_s": sm_blocks / (sm_ms / 1e3),
+                            "alu_frac": sm_blocks / (sm_ms / 1e3) / PHILOX_PEAK_BLOCKS,
+                            "launches_per_call": stats["launches"] / max(1, stats["calls"]) if
+                            stats.get("calls") else None,
+                            "rounds_per_call": stats["rounds"] / max(1, stats["calls"]) if
+                            stats.get("calls") else None},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "resnet" and args.impl != "reference":
@@ -562,6 +662,9 @@ def main():
         return
     if args.workload == "batched" and args.impl != "reference":
         run_batched(args)
+        return
+    if args.workload == "approx" and args.impl != "reference":
+        run_approx(args)
         return
     if args.impl == "reference":
         run_reference(args)

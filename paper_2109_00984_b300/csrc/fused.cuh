@@ -23,18 +23,26 @@ __device__ __forceinline__ Quad4 quad_gen(u64 seed, u64 op0, u64 w0, u64 op1, u6
   const u64 op = j == 0 ? op0 : j == 1 ? op1 : j == 2 ? op2 : op3;
   const u64 wd = j == 0 ? w0 : j == 1 ? w1 : j == 2 ? w2 : w3;
   const u64x4 b = prg_block(seed, op, wd, blk);
-  const int base = (threadIdx.x & 31) & ~3;
+  // 4 x 4 transpose across the quad (lane j holds block j, wants word j of
+  // blocks 0..3): two butterfly stages over lane bits 1 and 2, each swapping
+  // the half of the words whose index bit differs from the lane bit.
+  u64 a[4] = {b.v[0], b.v[1], b.v[2], b.v[3]};
+#pragma unroll
+  for (int m = 1; m <= 2; m <<= 1) {
+    const bool hi = (j & m) != 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k & m) continue;
+      const u64 t = __shfl_xor_sync(0xffffffffu, hi ? a[k] : a[k | m], m);
+      if (hi)
+        a[k] = t;
+      else
+        a[k | m] = t;
+    }
+  }
   Quad4 q;
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    u64 mine = 0;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const u64 v = __shfl_sync(0xffffffffu, b.v[w], base + s);
-      if (w == j) mine = v;
-    }
-    q.w[s] = mine;
-  }
+  for (int s = 0; s < 4; ++s) q.w[s] = a[s];
   return q;
 }
 
