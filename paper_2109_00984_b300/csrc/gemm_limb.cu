@@ -515,43 +515,67 @@ __global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
 
 // B side of a convolution, gathered straight from the data (implicit im2col):
 // the same tiling and stores as limb_planes_b, with element (k', n) read at its
-// data position instead of from a materialised im2col matrix.
+// data position instead of from a materialised im2col matrix.  The CTA's 64 k'
+// are decoded once into a shared tap table (offset ci h w + r w + s, r, s and
+// the source pair); column n = (b, oh, ow) is decoded once per thread, so an
+// element costs two bounds checks and an add.
 __global__ void __launch_bounds__(256) limb_planes_b_conv(const ConvGather cg, int job,
                                                            __nv_bfloat16* out, i64 N, i64 K,
                                                            i64 Kp) {
   __shared__ uint32_t tile[8][PB_TN][PB_ROW];
+  __shared__ i64 tap_off[PB_TK];
+  __shared__ int tap_r[PB_TK], tap_s[PB_TK], tap_src[PB_TK];  // src: 0 pair 1, 1 pair 2, -1 none
   const mpc_conv_desc& d = cg.d;
   const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
-  const i64 n = n0 + nl;
-  // Output column n -> (b, oh, ow).
-  const i64 ow = n % cg.wo, oh = (n / cg.wo) % cg.ho, b = n / (cg.wo * cg.ho);
   const u64* src2 = cg.src2[job];
+  if (tid < PB_TK) {
+    i64 k = k0 + tid;
+    int src = 0;
+    if (k >= K) {
+      k -= K;
+      src = 1;
+    }
+    if (k >= K || (src == 1 && !src2)) {
+      tap_src[tid] = -1;
+      tap_off[tid] = 0;
+      tap_r[tid] = tap_s[tid] = 0;
+    } else {
+      const i64 s_ = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
+      tap_src[tid] = src;
+      tap_off[tid] = (ci * d.h + r) * d.w + s_;
+      tap_r[tid] = (int)r;
+      tap_s[tid] = (int)s_;
+    }
+  }
+  // Output column n -> (b, oh, ow), and the data offset of its window origin.
+  const i64 n = n0 + nl;
+  const bool n_ok = n < N;
+  const i64 ow = n % cg.wo, oh = (n / cg.wo) % cg.ho, b = n / (cg.wo * cg.ho);
+  const i64 oy = oh * d.stride_h - d.pad_h, ox = ow * d.stride_w - d.pad_w;
+  const i64 base = (b * d.c_in * d.h + oy) * d.w + ox;
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int kl = 2 * (kq + 8 * j);
     u64 v[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      i64 k = k0 + kl + e;
+      const int t = kl + e;
+      const int src = tap_src[t];
       v[e] = 0;
-      const bool first = k < K;
-      if (!first) k -= K;
-      if (n < N && k < K && (first || src2)) {
-        const i64 s_ = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
-        const i64 y = oh * d.stride_h + r - d.pad_h, x = ow * d.stride_w + s_ - d.pad_w;
-        if (y >= 0 && y < d.h && x >= 0 && x < d.w) {
-          const i64 off = ((b * d.c_in + ci) * d.h + y) * d.w + x;
-          if (first) {
-            u64 acc = 0;
-            for (int q = 0; q < cg.n1; ++q) {
-              acc += cg.src1[q * cg.stride1 + off];
-              if (cg.sub1) acc -= cg.sub1[q * cg.stride1 + off];
-            }
-            v[e] = acc;
-          } else {
-            v[e] = src2[off];
+      const i64 y = oy + tap_r[t], x = ox + tap_s[t];
+      if (n_ok && src >= 0 && y >= 0 && y < d.h && x >= 0 && x < d.w) {
+        const i64 off = base + tap_off[t];
+        if (src == 0) {
+          u64 acc = 0;
+          for (int q = 0; q < cg.n1; ++q) {
+            acc += cg.src1[q * cg.stride1 + off];
+            if (cg.sub1) acc -= cg.sub1[q * cg.stride1 + off];
           }
+          v[e] = acc;
+        } else {
+          v[e] = src2[off];
         }
       }
     }
