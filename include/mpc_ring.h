@@ -134,6 +134,11 @@ int mpc_reset_stats(void);
 int mpc_profile_enable(int on);
 int mpc_profile_reset(void);
 int mpc_profile_read(const char* kernel, uint64_t* launches, double* total_ms);
+/* The union of the intervals of those launches (ms): the time during which
+ * at least one launch of `kernel` was running on any stream.  Launches that
+ * overlap (e.g. the same kernel on a dealer stream and the main stream) count
+ * once, so work / busy time is the kernel's throughput while it runs. */
+int mpc_profile_busy(const char* kernel, double* busy_ms);
 
 /* ---- sharing / reveal (§5.1, App. D.1.1) --------------------------------- */
 

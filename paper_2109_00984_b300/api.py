@@ -107,6 +107,13 @@ def profile_read(kernel):
     return int(n.value), float(ms.value)
 
 
+def profile_busy(kernel):
+    """Union of the device intervals of a timed kernel's launches (ms), over all streams."""
+    ms = ctypes.c_double()
+    _check(_L().mpc_profile_busy(kernel.encode(), ctypes.byref(ms)))
+    return float(ms.value)
+
+
 # ---- sharing / reveal ---------------------------------------------------------------
 def ring_share(x, P, src, seed, op_id, frac_bits=16, out=None):
     """Encode float64 reals x (CUDA) and share among P parties -> [P, *x.shape]."""

@@ -4,6 +4,7 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -175,6 +176,42 @@ int mpc_profile_read(const char* kernel, uint64_t* launches, double* total_ms) {
     }
     *launches = ps.used;
   }
+  return MPC_OK;
+}
+
+int mpc_profile_busy(const char* kernel, double* busy_ms) {
+  MPC_REQUIRE(kernel && busy_ms, "null pointer");
+  std::lock_guard<std::mutex> lk(mpc::g_prof_mu);
+  *busy_ms = 0.0;
+  std::vector<std::pair<double, double>> iv;
+  cudaEvent_t ref = nullptr;
+  for (auto& ps : mpc::g_prof) {
+    if (ps.name != kernel) continue;
+    for (size_t i = 0; i < ps.used; ++i) {
+      cudaError_t e = cudaEventSynchronize(ps.pairs[i].second);
+      if (e != cudaSuccess) return mpc::fail(MPC_ECUDA, "profile sync: %s", cudaGetErrorString(e));
+      if (!ref) ref = ps.pairs[i].first;
+      float a = 0.f, b = 0.f;
+      e = cudaEventElapsedTime(&a, ref, ps.pairs[i].first);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ref, ps.pairs[i].second);
+      if (e != cudaSuccess) return mpc::fail(MPC_ECUDA, "profile read: %s", cudaGetErrorString(e));
+      iv.emplace_back((double)a, (double)b);
+    }
+  }
+  std::sort(iv.begin(), iv.end());
+  double cur_a = 0.0, cur_b = 0.0;
+  bool open = false;
+  for (const auto& x : iv) {
+    if (open && x.first <= cur_b) {
+      cur_b = std::max(cur_b, x.second);
+    } else {
+      if (open) *busy_ms += cur_b - cur_a;
+      cur_a = x.first;
+      cur_b = x.second;
+      open = true;
+    }
+  }
+  if (open) *busy_ms += cur_b - cur_a;
   return MPC_OK;
 }
 
