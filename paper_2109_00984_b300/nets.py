@@ -75,7 +75,12 @@ class PrivateConv1dStack:
             self.bufs.append(b)
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         self.dealer_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-        self.dealer_stream = torch.cuda.Stream(device=dev) if self.overlap_dealer else None
+        # The online phase is the critical path: it runs on a high-priority stream,
+        # the dealer on a low-priority one, so freed SMs go to the online kernels.
+        self.dealer_stream = torch.cuda.Stream(device=dev, priority=0) if self.overlap_dealer \
+            else None
+        self.online_stream = torch.cuda.Stream(device=dev, priority=-5) if self.overlap_dealer \
+            else None
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
                                     dtype=torch.float64, device=dev)
 
@@ -94,6 +99,17 @@ class PrivateConv1dStack:
                     ev = torch.cuda.Event()
                     ev.record(ds)
                     ready.append(ev)
+        if self.overlap_dealer:
+            on = self.online_stream
+            on.wait_stream(main)
+            with torch.cuda.stream(on):
+                X = self._online(x, schedule, on, ready)
+            main.wait_stream(on)
+            return X
+        return self._online(x, schedule, main, ready)
+
+    def _online(self, x, schedule, main, ready):
+        seed = schedule["seed"]
         api.ring_share(x, self.P, 0, seed, schedule["input_op"], self.frac_bits, out=self.X0)
         X = self.X0
         for l, (d, b) in enumerate(zip(self.descs, self.bufs)):

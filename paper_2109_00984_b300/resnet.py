@@ -30,7 +30,11 @@ class PrivateResNet18:
         self.P = 2
         self.fused_relu = fused_relu
         self.overlap_dealer = overlap_dealer
-        self.dealer_stream = torch.cuda.Stream(device=device) if overlap_dealer else None
+        # Online phase on a high-priority stream, dealer on a low-priority one.
+        self.dealer_stream = torch.cuda.Stream(device=device, priority=0) if overlap_dealer \
+            else None
+        self.online_stream = torch.cuda.Stream(device=device, priority=-5) if overlap_dealer \
+            else None
         self.dealer_ws = torch.empty(1, dtype=torch.uint8, device=device)
         self.layers = layers
         self.algo = algo
@@ -168,13 +172,24 @@ class PrivateResNet18:
     # ---- forward ----------------------------------------------------------------------
     def forward(self, x, schedule):
         """x: float64 CUDA images (N, 3, H, W).  Returns logit shares [2, N, classes]."""
-        ops = schedule["ops"]
         self._triples = {}
         if self.overlap_dealer:
+            main = torch.cuda.current_stream()
             ds = self.dealer_stream
-            ds.wait_stream(torch.cuda.current_stream())
+            ds.wait_stream(main)
             with torch.cuda.stream(ds):
                 self._triples = self._deal_all(tuple(x.shape), schedule)
+            on = self.online_stream
+            on.wait_stream(main)
+            with torch.cuda.stream(on):
+                X = self._online(x, schedule)
+                X.record_stream(main)
+            main.wait_stream(on)
+            return X
+        return self._online(x, schedule)
+
+    def _online(self, x, schedule):
+        ops = schedule["ops"]
         X = api.ring_share(x, self.P, 0, self.seed, ops["input"], self.frac_bits)
         for layer in self.layers:
             kind, name = layer[0], layer[1]
