@@ -10,27 +10,33 @@
 //    exact bf16 (a "plane" holds one digit index of a whole matrix);
 //  * Z = sum_{i+j<8} 2^(8(i+j)) A_i B_j (mod 2^64): only the 36 digit pairs
 //    with i + j < 8 can reach the low 64 bits;
-//  * pairs with the same shift s = i + j share one fp32 TMEM accumulator
-//    (8 accumulators of 128 x 64 fill all 512 TMEM columns);
+//  * pairs with the same shift s = i + j share one fp32 TMEM accumulator.  A
+//    tile is 128 x 128 and runs in two passes over its K range: pass 0 the
+//    shifts 0..3 (digit planes 0..3 only), pass 1 the shifts 4..7 (all planes),
+//    four accumulators of 128 x 128 per pass filling the 512 TMEM columns.
+//    With N = 128 an MMA reads 8 KiB of operands from shared memory per
+//    128 x 128 x 16 MACs, which the tensor core's shared-memory port sustains at
+//    full rate (N = 64 with eight accumulators would read 6 KiB per half the
+//    work and cap the tensor pipe near two thirds of its peak);
 //  * |d_i d_j| <= 2^14 and at most 8 pairs share a shift, so 128 K-steps keep
 //    every partial sum within 2^24 where fp32 holds integers exactly.  Each
 //    accumulator is therefore drained every 8 sub-steps of K = 16 (chunks
-//    staggered by shift, so one drain overlaps the MMAs of the other seven)
-//    into a 64-bit integer register sum R += int(acc_s) << 8s;
+//    staggered by accumulator, one drain every other sub-step) into a 64-bit
+//    integer register sum R += int(acc_s) << 8s;
 //  * the epilogue adds C, applies the optional truncation and stores.
 //
 // Operands arrive as planes written by limb_planes_{a,b}: A as [8][M][Kp]
 // and B transposed as [8][N][Kp] (both K-major), with K-concatenated operand
 // pairs (Z = C + A1 B1 + A2 B2 is one GEMM over [A1 | A2] and [B1 ; B2]).
 //
-// Warp roles (416 threads): warp 0 issues TMA loads (one thread); warps 1-4
-// each issue the MMAs of two shifts, {w, 7 - w}, 9 per K sub-step (one thread
-// per warp: a single issuing thread cannot keep the tensor pipe busy with
-// N = 64 MMAs); warp 1 also allocates TMEM; warps 5-12 drain TMEM, two per
-// lane quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each, and
-// write the output.  Every wait is
-// bounded: on a timeout the CTA records MPC_ETIMEOUT, waits (bounded) for its
-// own copies and MMAs, frees TMEM and returns.
+// Warp roles (640 threads): warps 0-3 each issue the MMAs of one accumulator
+// slot q (shift q in pass 0, 4 + q in pass 1), one thread per warp; that
+// thread of warp 0 also issues the TMA loads, STAGES - 1 sub-steps ahead of
+// its own MMAs; warp 0 allocates TMEM; warps 4-19 drain TMEM, four per lane
+// quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each, and write
+// the output.  Every wait is bounded: on a timeout the CTA records
+// MPC_ETIMEOUT, waits (bounded) for its own copies and MMAs, frees TMEM and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -46,17 +52,19 @@ namespace mpc {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, KS = 16, STAGES = 4, NSHIFT = 8, CHUNK = 8;
-constexpr int A_PLANE_BYTES = BM * KS * 2;             // 4 KiB
-constexpr int B_PLANE_BYTES = BN * KS * 2;             // 2 KiB
-constexpr int A_STAGE_BYTES = NSHIFT * A_PLANE_BYTES;  // 32 KiB
-constexpr int B_STAGE_BYTES = NSHIFT * B_PLANE_BYTES;  // 16 KiB
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int BM = 128, BN = 128, KS = 16, STAGES = 3, NPLANE = 8, NSLOT = 4, CHUNK = 8;
+constexpr int PLANE_BYTES = BM * KS * 2;               // 4 KiB: one digit plane of a tile
+constexpr int A_STAGE_BYTES = NPLANE * PLANE_BYTES;    // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_STAGE_BYTES;         // A then B planes: 64 KiB
+constexpr int HALF_LOAD_BYTES = 4 * PLANE_BYTES;       // one TMA box: 4 planes
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int kIssuers = 4;      // MMA-issuing warps (1..4)
-constexpr int kDrainWarps = 8;   // TMEM drain / epilogue warps (5..12)
-constexpr int kThreads = 32 * (1 + kIssuers + kDrainWarps);
+constexpr int kIssuers = 4;      // MMA-issuing warps (0..3); warp 0 also loads
+constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps (4..19)
+// 20 warps, 5 per SM sub-partition: up to 96 registers per thread (the drain
+// warps hold 32 64-bit sums each).
+constexpr int kThreads = 32 * (kIssuers + kDrainWarps);
 constexpr uint32_t TMEM_COLS = 512;
+static_assert(BM == BN, "A and B plane tiles share one layout");
 // Instruction descriptor, kind::f16: D f32 (bit 4), A bf16 (bits 7-9 = 1),
 // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -171,75 +179,115 @@ __device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
   return d;
 }
 
-#define TMEM_LD_X32(taddr, r)                                                                  \
+#define TMEM_LD_X16(taddr, r)                                                                  \
   asm volatile(                                                                                \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "  \
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "  \
-      "%28, %29, %30, %31}, [%32];"                                                             \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "  \
+      "%11, %12, %13, %14, %15}, [%16];"                                                        \
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),    \
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),             \
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),          \
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),          \
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),          \
-        "=r"(r[31])                                                                            \
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                                                  \
       : "r"(taddr))
 
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The s + 1 digit-pair MMAs of shift S: D += sum_{i <= S} A_i B_{S - i}.
-template <int S>
-__device__ __forceinline__ void issue_shift_t(uint32_t d, uint64_t a0, uint64_t b0, bool start) {
-  tc_mma(d, a0, b0 + (uint64_t)(S * (B_PLANE_BYTES >> 4)), start ? 0u : 1u);
-#pragma unroll
-  for (int i = 1; i <= S; ++i)
-    tc_mma(d, a0 + (uint64_t)(i * (A_PLANE_BYTES >> 4)),
-           b0 + (uint64_t)((S - i) * (B_PLANE_BYTES >> 4)), 1u);
+// The s + 1 digit-pair MMAs of shift s: D += sum_{i <= s} A_i B_{s - i}.
+__device__ __forceinline__ void issue_shift(uint32_t d, uint64_t a0, uint64_t b0, int s,
+                                            bool start) {
+  tc_mma(d, a0, b0 + (uint64_t)(s * (PLANE_BYTES >> 4)), start ? 0u : 1u);
+  for (int i = 1; i <= s; ++i)
+    tc_mma(d, a0 + (uint64_t)(i * (PLANE_BYTES >> 4)),
+           b0 + (uint64_t)((s - i) * (PLANE_BYTES >> 4)), 1u);
 }
 
-// Shift s's chunk ends after sub-step t when t = s - 1 (mod CHUNK), or at the
-// end t_end - 1 of the CTA's K range.
-__device__ __forceinline__ bool chunk_ends(int t, int s, int t_end) {
-  return (t % CHUNK) == ((s + CHUNK - 1) % CHUNK) || t == t_end - 1;
+// The chunk of accumulator slot q ends after sub-step t when t = 2q + 1
+// (mod 8), or at the end t_end - 1 of the K range: one drain every other
+// sub-step.
+__device__ __forceinline__ bool chunk_ends(int t, int q, int t_end) {
+  return (t & (CHUNK - 1)) == 2 * q + 1 || t == t_end - 1;
 }
 
-// The two shifts owned by MMA-issuer warp w: {w, 7 - w}, 9 digit-pair MMAs
-// per K sub-step for every issuer.
-template <int W>
-__device__ __forceinline__ void issuer_loop(const LimbParams& p, uint32_t sbase, uint32_t tmem,
-                                            int t_begin, int t_end, uint64_t* full_bar,
-                                            uint64_t* empty_bar, uint64_t* accf_bar,
-                                            uint64_t* acce_bar, volatile int* abort_flag) {
-  constexpr int S0 = W, S1 = NSHIFT - 1 - W;
-  uint32_t chunks0 = 0, chunks1 = 0;
-  for (int t = t_begin; t < t_end; ++t) {
-    const int st = (t - t_begin) % STAGES;
-    const uint32_t ph = (uint32_t)((t - t_begin) / STAGES) & 1u;
+// TMA loads of sub-step g (over both passes): pass 0 digit planes 0..3 of A and
+// B, pass 1 all eight.  Waits (bounded) until every issuer released the stage.
+struct Loader {
+  const LimbParams* p;
+  uint32_t sbase;
+  int job, m0, n0, t_begin, steps;
+  uint64_t *full_bar, *empty_bar;
+  volatile int* abort_flag;
+  int last_g[STAGES];
+  __device__ __forceinline__ bool load(int g) {
+    const int pass = g >= steps;
+    const int t = t_begin + g - pass * steps;
+    const int st = g % STAGES;
+    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+    if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) return false;
+    mbar_arrive_expect_tx(&full_bar[st], (pass ? 4 : 2) * HALF_LOAD_BYTES);
+    const uint32_t a_dst = sbase + st * STAGE_BYTES;
+    const uint32_t b_dst = a_dst + A_STAGE_BYTES;
+    tma_load_3d(a_dst, &p->tmA[job], &full_bar[st], t * KS, m0, 0);
+    tma_load_3d(b_dst, &p->tmB[job], &full_bar[st], t * KS, n0, 0);
+    if (pass) {
+      tma_load_3d(a_dst + HALF_LOAD_BYTES, &p->tmA[job], &full_bar[st], t * KS, m0, 4);
+      tma_load_3d(b_dst + HALF_LOAD_BYTES, &p->tmB[job], &full_bar[st], t * KS, n0, 4);
+    }
+    last_g[st] = g;
+    return true;
+  }
+  // Copies in flight must land before the CTA can leave (bounded).
+  __device__ __forceinline__ void drain_copies() {
+    for (int i = 0; i < STAGES; ++i) {
+      if (last_g[i] < 0) continue;
+      const uint32_t ph = (uint32_t)(last_g[i] / STAGES) & 1u;
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(&full_bar[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  }
+};
+
+// MMA issuer of accumulator slot q: shift q in pass 0, 4 + q in pass 1.  g
+// counts sub-steps over both passes (pipeline stage and phase); a chunk starts
+// at the range's first sub-step or right after the previous one ended, and
+// waits until the drain warps have read the slot's previous chunk (which may
+// belong to pass 0).  With a Loader (slot 0) the thread also keeps the TMA
+// loads STAGES - 1 sub-steps ahead: the load of g + STAGES - 1 reuses the
+// stage of g - 1, which this thread has already released.
+__device__ __forceinline__ void issuer_loop(int q, uint32_t sbase, uint32_t tmem, int t_begin,
+                                            int t_end, uint64_t* full_bar, uint64_t* empty_bar,
+                                            uint64_t* accf_bar, uint64_t* acce_bar,
+                                            volatile int* abort_flag, Loader* ld) {
+  const int steps = t_end - t_begin, total = 2 * steps;
+  int gl = 0;
+  if (ld)
+    for (; gl < STAGES - 1 && gl < total; ++gl)
+      if (!ld->load(gl)) return;
+  uint32_t chunks = 0;
+  const uint32_t d = tmem + (uint32_t)(q * BN);
+  for (int g = 0; g < total; ++g) {
+    if (ld && gl < total) {
+      if (!ld->load(gl)) return;
+      ++gl;
+    }
+    const int pass = g >= steps;
+    const int t = t_begin + g - pass * steps;
+    const int shift = 4 * pass + q;
+    const int st = g % STAGES;
+    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
     if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
     tc_fence_after();
     const uint64_t a0 = smem_desc_sw32(sbase + st * STAGE_BYTES);
     const uint64_t b0 = smem_desc_sw32(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
-    // A chunk of shift s starts right after one ended (or at t = t_begin).
-    const bool start0 = (t == t_begin) || ((t - 1) % CHUNK) == ((S0 + CHUNK - 1) % CHUNK);
-    const bool start1 = (t == t_begin) || ((t - 1) % CHUNK) == ((S1 + CHUNK - 1) % CHUNK);
-    if (start0 && t > t_begin) {
-      if (!mbar_wait(&acce_bar[S0], (chunks0 - 1u) & 1u, abort_flag)) return;
+    const bool start = (t == t_begin) || chunk_ends(t - 1, q, t_end);
+    if (start && chunks > 0) {
+      if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return;
       tc_fence_after();
     }
-    issue_shift_t<S0>(tmem + (uint32_t)(S0 * BN), a0, b0, start0);
-    if (chunk_ends(t, S0, t_end)) {
-      tc_commit(&accf_bar[S0]);
-      chunks0++;
-    }
-    if (start1 && t > t_begin) {
-      if (!mbar_wait(&acce_bar[S1], (chunks1 - 1u) & 1u, abort_flag)) return;
-      tc_fence_after();
-    }
-    issue_shift_t<S1>(tmem + (uint32_t)(S1 * BN), a0, b0, start1);
-    if (chunk_ends(t, S1, t_end)) {
-      tc_commit(&accf_bar[S1]);
-      chunks1++;
+    issue_shift(d, a0, b0, shift, start);
+    if (chunk_ends(t, q, t_end)) {
+      tc_commit(&accf_bar[q]);
+      chunks++;
     }
     tc_commit(&empty_bar[st]);
   }
@@ -248,14 +296,14 @@ __device__ __forceinline__ void issuer_loop(const LimbParams& p, uint32_t sbase,
 __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t accf_bar[NSHIFT], acce_bar[NSHIFT], done_bar;
+  __shared__ __align__(8) uint64_t accf_bar[NSLOT], acce_bar[NSLOT], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int job = blockIdx.z / p.splits, split = blockIdx.z % p.splits;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  // This CTA's K sub-steps [t_begin, t_end).
+  // This CTA's K sub-steps [t_begin, t_end), run once per pass.
   const int t_begin = (int)((i64)p.T * split / p.splits);
   const int t_end = (int)((i64)p.T * (split + 1) / p.splits);
   const uint32_t sbase = (smem_u32(dsmem) + 1023u) & ~1023u;
@@ -265,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], kIssuers);
     }
-    for (int i = 0; i < NSHIFT; ++i) {
+    for (int i = 0; i < NSLOT; ++i) {
       mbar_init(&accf_bar[i], 1);
       mbar_init(&acce_bar[i], kDrainWarps);
     }
@@ -277,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmA[job])));
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmB[job])));
   }
-  if (warp == 1) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
                  "r"(TMEM_COLS));
@@ -287,44 +335,26 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  const int steps = t_end - t_begin;
 
-  if (warp == 0) {
+  if (warp < kIssuers) {
     if (lane == 0) {
-      // ---- TMA producer ----
-      int last_t[STAGES];
-      for (int i = 0; i < STAGES; ++i) last_t[i] = -1;
-      for (int t = t_begin; t < t_end; ++t) {
-        const int st = (t - t_begin) % STAGES;
-        const uint32_t ph = (uint32_t)((t - t_begin) / STAGES) & 1u;
-        if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag)) break;
-        mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
-        const uint32_t a_dst = sbase + st * STAGE_BYTES;
-        tma_load_3d(a_dst, &p.tmA[job], &full_bar[st], t * KS, m0, 0);
-        tma_load_3d(a_dst + A_STAGE_BYTES, &p.tmB[job], &full_bar[st], t * KS, n0, 0);
-        last_t[st] = t - t_begin;
-      }
-      // Copies in flight must land before the CTA can leave (bounded).
-      for (int i = 0; i < STAGES; ++i) {
-        if (last_t[i] < 0) continue;
-        const uint32_t ph = (uint32_t)(last_t[i] / STAGES) & 1u;
-        const unsigned long long t0 = globaltimer();
-        while (!mbar_try_wait(&full_bar[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
-        }
-      }
-    }
-  } else if (warp <= kIssuers) {
-    if (lane == 0) {
-      // ---- MMA issuers: warp 1 + w owns shifts {w, 7 - w} ----
-      switch (warp - 1) {
-        case 0: issuer_loop<0>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
-                               acce_bar, &abort_flag); break;
-        case 1: issuer_loop<1>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
-                               acce_bar, &abort_flag); break;
-        case 2: issuer_loop<2>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
-                               acce_bar, &abort_flag); break;
-        default: issuer_loop<3>(p, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar,
-                                acce_bar, &abort_flag); break;
-      }
+      // ---- MMA issuers: warp q owns accumulator slot q; warp 0 also loads ----
+      Loader ldr;
+      ldr.p = &p;
+      ldr.sbase = sbase;
+      ldr.job = job;
+      ldr.m0 = m0;
+      ldr.n0 = n0;
+      ldr.t_begin = t_begin;
+      ldr.steps = steps;
+      ldr.full_bar = full_bar;
+      ldr.empty_bar = empty_bar;
+      ldr.abort_flag = &abort_flag;
+      for (int i = 0; i < STAGES; ++i) ldr.last_g[i] = -1;
+      issuer_loop(warp, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar, acce_bar,
+                  &abort_flag, warp == 0 ? &ldr : nullptr);
+      if (warp == 0) ldr.drain_copies();
       // All of this issuer's MMAs must finish before TMEM is released (bounded).
       tc_commit(&done_bar);
       const unsigned long long t0 = globaltimer();
@@ -332,43 +362,53 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
       }
     }
   } else {
-    // ---- TMEM drain + epilogue: 8 warps, two per TMEM lane quadrant ----
-    const int ew = warp - 1 - kIssuers;           // 0..7
-    const int q = warp & 3;                       // lane quadrant this warp may access
-    const int half = ew >> 2;                     // which 32 of the 64 columns
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    // ---- TMEM drain + epilogue: 16 warps, four per TMEM lane quadrant ----
+    const int ew = warp - kIssuers;               // 0..15
+    const int quad = warp & 3;                    // lane quadrant this warp may access
+    const int cblk = ew >> 2;                     // which 32 of the 128 columns
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cblk * 32);
     u64 R[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) R[j] = 0;
-    uint32_t chunks[NSHIFT];
-#pragma unroll
-    for (int s = 0; s < NSHIFT; ++s) chunks[s] = 0;
+    uint32_t parity = 0;  // bit q: parity of the next chunk of slot q
     bool ok = true;
-    for (int t = t_begin; t < t_end && ok; ++t) {
-      for (int s = 0; s < NSHIFT; ++s) {
-        if (!chunk_ends(t, s, t_end)) continue;
-        if (!mbar_wait(&accf_bar[s], chunks[s] & 1u, &abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        uint32_t v[32];
-        TMEM_LD_X32(lane_base + (uint32_t)(s * BN), v);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acce_bar[s]);
-        chunks[s]++;
-        const int sh = 8 * s;
+    // Drain slot q's finished chunk of shift sh / 8 into R.
+    auto drain = [&](int q, int sh) -> bool {
+      if (!mbar_wait(&accf_bar[q], (parity >> q) & 1u, &abort_flag)) return false;
+      tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+      for (int h = 0; h < 2; ++h) {  // two loads of 16 columns: 80 live registers, not 96
+        uint32_t v[16];
+        TMEM_LD_X16(lane_base + (uint32_t)(q * BN + 16 * h), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
           const int iv = __float2int_rz(__uint_as_float(v[j]));
-          R[j] += (u64)(i64)iv << sh;
+          R[16 * h + j] += (u64)(i64)iv << sh;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[q]);
+      parity ^= 1u << q;
+      return true;
+    };
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        if (t < t_end - 1) {
+          if (t & 1) {
+            const int q = (t & (CHUNK - 1)) >> 1;  // t = 2q + 1 (mod 8)
+            ok = drain(q, 8 * (4 * pass + q));
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NSLOT; ++q)
+            if (ok) ok = drain(q, 8 * (4 * pass + q));
         }
       }
     }
-    const i64 row = (i64)m0 + q * 32 + lane;
-    const int c0 = n0 + half * 32;
+    const i64 row = (i64)m0 + quad * 32 + lane;
+    const int c0 = n0 + cblk * 32;
     if (ok && !abort_flag && row < p.M) {
       if (p.splits > 1) {
         u64* part = p.partial + ((i64)split * p.njobs + job) * p.M * p.N + row * p.N;
@@ -396,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   tc_fence_before();
   __syncthreads();
   if (abort_flag && threadIdx.x == 0) record_status(p.status, MPC_ETIMEOUT);
-  if (warp == 1) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS));
@@ -612,11 +652,11 @@ int get_encoder() {
   return g_encode ? MPC_OK : fail(MPC_ECUDA, "cuTensorMapEncodeTiled unavailable");
 }
 
-// 3-D map over planes [8][rows][Kp] bf16 with a {16, box_rows, 8} box, 32-byte swizzle.
+// 3-D map over planes [8][rows][Kp] bf16 with a {16, box_rows, 4} box, 32-byte swizzle.
 int encode_planes(CUtensorMap* tm, const void* base, i64 rows, i64 Kp, int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 8};
   cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 8};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 4};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -633,7 +673,7 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs) {
   const i64 tiles = ceil_div(M, BM) * ceil_div(N, BN) * njobs;
-  return choose_splits(tiles, padded_k(K, npairs) / KS, 32);
+  return choose_splits(tiles, padded_k(K, npairs) / KS, 16);
 }
 
 bool limb_supported(i64 M, i64 N, i64 K) {
