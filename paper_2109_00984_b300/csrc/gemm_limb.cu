@@ -445,34 +445,39 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
 
 // ---- plane pre-pass ---------------------------------------------------------------------
 // Balanced base-256 digits of v: v = sum_i d_i 2^(8i) mod 2^64, d_i in [-128, 127].
-__device__ __forceinline__ void balanced_digits(u64 v, int d[8]) {
-  int carry = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int t = (int)((v >> (8 * i)) & 255ull) + carry;
-    carry = t >= 128;
-    d[i] = t - (carry << 8);
-  }
+// With u = v + 0x8080808080808080 (mod 2^64), byte i of u is d_i + 128: adding
+// 128 to every digit position absorbs all the carries of the balanced form.
+// For a byte b, the float with bits 0x4B000000 | b is 2^23 + b; subtracting
+// 2^23 + 128 gives d = b - 128 exactly, and since |d| <= 128 has at most 8
+// significant bits its bf16 is the upper half of that float.  digit_bits(u, i)
+// returns those float bits (bf16 in the upper 16 bits).
+__device__ __forceinline__ uint32_t digit_bits(u64 u, int i) {
+  const uint32_t w = (uint32_t)(u >> (i < 4 ? 0 : 32));
+  // bytes, high to low: 0x4B, 0, 0, byte (i mod 4) of w
+  const uint32_t f = __byte_perm(w, 0x4B000000u, 0x7440u | (uint32_t)(i & 3));
+  return __float_as_uint(__uint_as_float(f) - 8388736.0f);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-  const __nv_bfloat16 a = __float2bfloat16_rn((float)lo), b = __float2bfloat16_rn((float)hi);
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+__device__ __forceinline__ u64 digit_base(u64 v) { return v + 0x8080808080808080ull; }
+
+// Two bf16 digits packed low | high from their float bits.
+__device__ __forceinline__ uint32_t pack_hi16(uint32_t lo_bits, uint32_t hi_bits) {
+  return __byte_perm(lo_bits, hi_bits, 0x7632u);
 }
 
 // Writes 8 consecutive k' of one row into the 8 planes of `out` ([8][rows][Kp]).
 __device__ __forceinline__ void write_planes(const u64 v[8], __nv_bfloat16* out, i64 rows,
                                              i64 row, i64 Kp, i64 k0) {
-  int d[8][8];  // [element][digit]
+  u64 u[8];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) balanced_digits(v[e], d[e]);
+  for (int e = 0; e < 8; ++e) u[e] = digit_base(v[e]);
 #pragma unroll
   for (int pl = 0; pl < 8; ++pl) {
     uint4 w;
-    w.x = pack_bf16x2(d[0][pl], d[1][pl]);
-    w.y = pack_bf16x2(d[2][pl], d[3][pl]);
-    w.z = pack_bf16x2(d[4][pl], d[5][pl]);
-    w.w = pack_bf16x2(d[6][pl], d[7][pl]);
+    w.x = pack_hi16(digit_bits(u[0], pl), digit_bits(u[1], pl));
+    w.y = pack_hi16(digit_bits(u[2], pl), digit_bits(u[3], pl));
+    w.z = pack_hi16(digit_bits(u[4], pl), digit_bits(u[5], pl));
+    w.w = pack_hi16(digit_bits(u[6], pl), digit_bits(u[7], pl));
     *reinterpret_cast<uint4*>(out + ((i64)pl * rows + row) * Kp + k0) = w;
   }
 }
@@ -483,13 +488,14 @@ struct PlaneJob {
   __nv_bfloat16* out;
 };
 
+struct PlaneJobs {
+  PlaneJob j[MPC_MAX_PARTIES];
+};
+
 // A side: X is [M][K] row-major; element (m, k') of [X1 | X2].
-__global__ void __launch_bounds__(256) limb_planes_a(PlaneJob j0,
-                                                      PlaneJob j1, PlaneJob j2, PlaneJob j3,
-                                                      PlaneJob j4, PlaneJob j5, PlaneJob j6,
-                                                      PlaneJob j7, i64 M, i64 K, i64 Kp) {
-  const PlaneJob js[8] = {j0, j1, j2, j3, j4, j5, j6, j7};
-  const PlaneJob& jb = js[blockIdx.y];
+__global__ void __launch_bounds__(256) limb_planes_a(const __grid_constant__ PlaneJobs js, i64 M,
+                                                      i64 K, i64 Kp) {
+  const PlaneJob& jb = js.j[blockIdx.y];
   const i64 kc = Kp / 8;
   const i64 total = M * kc;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
@@ -511,13 +517,10 @@ __global__ void __launch_bounds__(256) limb_planes_a(PlaneJob j0,
 // distinct banks), then each warp writes 128-byte runs of one plane row.
 constexpr int PB_TK = 64, PB_TN = 32, PB_ROW = PB_TK / 2 + 1;  // words per smem row
 
-__global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
-                                                      PlaneJob j1, PlaneJob j2, PlaneJob j3,
-                                                      PlaneJob j4, PlaneJob j5, PlaneJob j6,
-                                                      PlaneJob j7, i64 N, i64 K, i64 Kp) {
+__global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ PlaneJobs js, i64 N,
+                                                      i64 K, i64 Kp) {
   __shared__ uint32_t tile[8][PB_TN][PB_ROW];
-  const PlaneJob js[8] = {j0, j1, j2, j3, j4, j5, j6, j7};
-  const PlaneJob& jb = js[blockIdx.z];
+  const PlaneJob& jb = js.j[blockIdx.z];
   const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
   const i64 n = n0 + nl;
@@ -535,11 +538,10 @@ __global__ void __launch_bounds__(256) limb_planes_b(PlaneJob j0,
         else if (jb.X2 && k < 2 * K) v[e] = jb.X2[(k - K) * N + n];
       }
     }
-    int d0[8], d1[8];
-    balanced_digits(v[0], d0);
-    balanced_digits(v[1], d1);
+    const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
 #pragma unroll
-    for (int pl = 0; pl < 8; ++pl) tile[pl][nl][kl >> 1] = pack_bf16x2(d0[pl], d1[pl]);
+    for (int pl = 0; pl < 8; ++pl)
+      tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
   // Store phase: 8 planes x 32 rows; each warp writes whole 128-byte row runs.
@@ -619,11 +621,10 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const ConvGather cg, i
         }
       }
     }
-    int d0[8], d1[8];
-    balanced_digits(v[0], d0);
-    balanced_digits(v[1], d1);
+    const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
 #pragma unroll
-    for (int pl = 0; pl < 8; ++pl) tile[pl][nl][kl >> 1] = pack_bf16x2(d0[pl], d1[pl]);
+    for (int pl = 0; pl < 8; ++pl)
+      tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5;
@@ -708,7 +709,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   if (!st) return fail(MPC_ECUDA, "device status word unavailable");
 
   // Planes for every job.
-  PlaneJob ja[8] = {}, jbv[8] = {};
+  PlaneJobs ja = {}, jbv = {};
   char* w = static_cast<char*>(ws);
   LimbParams prm;
   memset(&prm, 0, sizeof(prm));
@@ -717,8 +718,8 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     w += al256((size_t)8 * g.M * Kp * 2);
     __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(w);
     w += al256((size_t)8 * g.N * Kp * 2);
-    ja[j] = PlaneJob{g.jobs[j].A1, g.jobs[j].A2, pa};
-    jbv[j] = PlaneJob{g.jobs[j].B1, g.jobs[j].B2, pb};
+    ja.j[j] = PlaneJob{g.jobs[j].A1, g.jobs[j].A2, pa};
+    jbv.j[j] = PlaneJob{g.jobs[j].B1, g.jobs[j].B2, pb};
     if (int rc = encode_planes(&prm.tmA[j], pa, g.M, Kp, BM)) return rc;
     if (int rc = encode_planes(&prm.tmB[j], pb, g.N, Kp, BN)) return rc;
     prm.C[j] = g.jobs[j].C;
@@ -730,18 +731,16 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     dim3 ga(grid_for(ta, 256, 148 * 16), g.njobs);
     dim3 gb((unsigned)ceil_div(Kp, PB_TK), (unsigned)ceil_div(g.N, PB_TN), g.njobs);
     if (ceil_div(g.N, PB_TN) > 65535) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
-    limb_planes_a<<<ga, 256, 0, s>>>(ja[0], ja[1], ja[2], ja[3], ja[4], ja[5], ja[6],
-                                     ja[7], g.M, g.K, Kp);
+    limb_planes_a<<<ga, 256, 0, s>>>(ja, g.M, g.K, Kp);
     if (int rc = check_launch("limb_planes_a")) return rc;
     if (g.gather) {
       for (int j = 0; j < g.njobs; ++j) {
         dim3 gj(gb.x, gb.y, 1);
-        limb_planes_b_conv<<<gj, 256, 0, s>>>(*g.gather, j, jbv[j].out, g.N, g.K, Kp);
+        limb_planes_b_conv<<<gj, 256, 0, s>>>(*g.gather, j, jbv.j[j].out, g.N, g.K, Kp);
         if (int rc = check_launch("limb_planes_b_conv")) return rc;
       }
     } else {
-      limb_planes_b<<<gb, 256, 0, s>>>(jbv[0], jbv[1], jbv[2], jbv[3], jbv[4], jbv[5],
-                                       jbv[6], jbv[7], g.N, g.K, Kp);
+      limb_planes_b<<<gb, 256, 0, s>>>(jbv, g.N, g.K, Kp);
       if (int rc = check_launch("limb_planes_b")) return rc;
     }
   }
