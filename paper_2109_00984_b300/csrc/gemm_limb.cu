@@ -71,14 +71,18 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
                            ((uint32_t)(BM >> 4) << 24);
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
+// Each operand pair has its own planes ([8][rows][K1p], K1p = K rounded up to
+// 16), so a pair that all jobs share (the opened E or F) is cut into digits
+// once: tmA[pair][job] / tmB[pair][job] of different jobs may map one buffer.
 struct LimbParams {
-  CUtensorMap tmA[MPC_MAX_PARTIES];
-  CUtensorMap tmB[MPC_MAX_PARTIES];
+  CUtensorMap tmA[2][MPC_MAX_PARTIES];
+  CUtensorMap tmB[2][MPC_MAX_PARTIES];
   const u64* C[MPC_MAX_PARTIES];
   u64* Z[MPC_MAX_PARTIES];
   u64* partial;  // split-K partial sums [splits][njobs][M][N] (splits > 1)
   i64 M, N, hw_out;
-  int T;  // K sub-steps of 16
+  int T;   // K sub-steps of 16 over both pairs
+  int T1;  // sub-steps of one pair
   int trunc_bits;
   int splits, njobs;
   int* status;
@@ -220,17 +224,21 @@ struct Loader {
   __device__ __forceinline__ bool load(int g) {
     const int pass = g >= steps;
     const int t = t_begin + g - pass * steps;
+    const int pair = t >= p->T1;
+    const int x = (t - pair * p->T1) * KS;
+    const CUtensorMap* ta = &p->tmA[pair][job];
+    const CUtensorMap* tb = &p->tmB[pair][job];
     const int st = g % STAGES;
     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
     if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) return false;
     mbar_arrive_expect_tx(&full_bar[st], (pass ? 4 : 2) * HALF_LOAD_BYTES);
     const uint32_t a_dst = sbase + st * STAGE_BYTES;
     const uint32_t b_dst = a_dst + A_STAGE_BYTES;
-    tma_load_3d(a_dst, &p->tmA[job], &full_bar[st], t * KS, m0, 0);
-    tma_load_3d(b_dst, &p->tmB[job], &full_bar[st], t * KS, n0, 0);
+    tma_load_3d(a_dst, ta, &full_bar[st], x, m0, 0);
+    tma_load_3d(b_dst, tb, &full_bar[st], x, n0, 0);
     if (pass) {
-      tma_load_3d(a_dst + HALF_LOAD_BYTES, &p->tmA[job], &full_bar[st], t * KS, m0, 4);
-      tma_load_3d(b_dst + HALF_LOAD_BYTES, &p->tmB[job], &full_bar[st], t * KS, n0, 4);
+      tma_load_3d(a_dst + HALF_LOAD_BYTES, ta, &full_bar[st], x, m0, 4);
+      tma_load_3d(b_dst + HALF_LOAD_BYTES, tb, &full_bar[st], x, n0, 4);
     }
     last_g[st] = g;
     return true;
@@ -322,8 +330,10 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
     // mpc_sync_status) makes every later CTA skip its work and exit at once.
     abort_flag = (*(volatile int*)p.status == MPC_ETIMEOUT) ? 1 : 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmA[job])));
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmB[job])));
+    for (int pr = 0; pr < 2; ++pr) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmA[pr][job])));
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.tmB[pr][job])));
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -489,7 +499,7 @@ struct PlaneJob {
 };
 
 struct PlaneJobs {
-  PlaneJob j[MPC_MAX_PARTIES];
+  PlaneJob j[2 * MPC_MAX_PARTIES];
 };
 
 // A side: X is [M][K] row-major; element (m, k') of [X1 | X2].
@@ -556,35 +566,34 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
 }
 
 // B side of a convolution, gathered straight from the data (implicit im2col):
-// the same tiling and stores as limb_planes_b, with element (k', n) read at its
-// data position instead of from a materialised im2col matrix.  The CTA's 64 k'
-// are decoded once into a shared tap table (offset ci h w + r w + s, r, s and
-// the source pair); column n = (b, oh, ow) is decoded once per thread, so an
-// element costs two bounds checks and an add.
-__global__ void __launch_bounds__(256) limb_planes_b_conv(const ConvGather cg, int job,
-                                                           __nv_bfloat16* out, i64 N, i64 K,
-                                                           i64 Kp) {
+// the same tiling and stores as limb_planes_b, with element (k, n) read at its
+// data position instead of from a materialised im2col matrix.  blockIdx.z = 0
+// writes pair 1 (the opened sum over src1 - sub1, shared by all jobs) to
+// outs.j[0].out; blockIdx.z = 1 + j writes job j's pair 2 (src2[j]) to
+// outs.j[1 + j].out.  The CTA's 64 k are decoded once into a shared tap table
+// (offset ci h w + r w + s, r, s); column n = (b, oh, ow) is decoded once per
+// thread, so an element costs two bounds checks and an add.
+__global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant__ ConvGather cg,
+                                                           const __grid_constant__ PlaneJobs outs,
+                                                           i64 N, i64 K, i64 Kp) {
   __shared__ uint32_t tile[8][PB_TN][PB_ROW];
   __shared__ i64 tap_off[PB_TK];
-  __shared__ int tap_r[PB_TK], tap_s[PB_TK], tap_src[PB_TK];  // src: 0 pair 1, 1 pair 2, -1 none
+  __shared__ int tap_r[PB_TK], tap_s[PB_TK], tap_ok[PB_TK];
   const mpc_conv_desc& d = cg.d;
+  const int z = blockIdx.z;
+  const u64* src2 = z > 0 ? cg.src2[z - 1] : nullptr;
+  __nv_bfloat16* out = outs.j[z].out;
   const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
-  const u64* src2 = cg.src2[job];
   if (tid < PB_TK) {
-    i64 k = k0 + tid;
-    int src = 0;
+    const i64 k = k0 + tid;
     if (k >= K) {
-      k -= K;
-      src = 1;
-    }
-    if (k >= K || (src == 1 && !src2)) {
-      tap_src[tid] = -1;
+      tap_ok[tid] = 0;
       tap_off[tid] = 0;
       tap_r[tid] = tap_s[tid] = 0;
     } else {
       const i64 s_ = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
-      tap_src[tid] = src;
+      tap_ok[tid] = 1;
       tap_off[tid] = (ci * d.h + r) * d.w + s_;
       tap_r[tid] = (int)r;
       tap_s[tid] = (int)s_;
@@ -604,12 +613,11 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const ConvGather cg, i
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int t = kl + e;
-      const int src = tap_src[t];
       v[e] = 0;
       const i64 y = oy + tap_r[t], x = ox + tap_s[t];
-      if (n_ok && src >= 0 && y >= 0 && y < d.h && x >= 0 && x < d.w) {
+      if (n_ok && tap_ok[t] && y >= 0 && y < d.h && x >= 0 && x < d.w) {
         const i64 off = base + tap_off[t];
-        if (src == 0) {
+        if (z == 0) {
           u64 acc = 0;
           for (int q = 0; q < cg.n1; ++q) {
             acc += cg.src1[q * cg.stride1 + off];
@@ -666,7 +674,8 @@ int encode_planes(CUtensorMap* tm, const void* base, i64 rows, i64 Kp, int box_r
   return r == CUDA_SUCCESS ? MPC_OK : fail(MPC_ECUDA, "tensor map encode failed (%d)", (int)r);
 }
 
-inline i64 padded_k(i64 K, int npairs) { return ceil_div(npairs * K, KS) * KS; }
+// K of one operand pair rounded up to whole sub-steps.
+inline i64 pair_k(i64 K) { return ceil_div(K, KS) * KS; }
 
 inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -674,7 +683,7 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs) {
   const i64 tiles = ceil_div(M, BM) * ceil_div(N, BN) * njobs;
-  return choose_splits(tiles, padded_k(K, npairs) / KS, 16);
+  return choose_splits(tiles, npairs * pair_k(K) / KS, 16);
 }
 
 bool limb_supported(i64 M, i64 N, i64 K) {
@@ -683,8 +692,9 @@ bool limb_supported(i64 M, i64 N, i64 K) {
 }
 
 size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs) {
-  const i64 Kp = padded_k(K, npairs);
-  return (size_t)njobs * (al256((size_t)8 * M * Kp * 2) + al256((size_t)8 * N * Kp * 2));
+  // Upper bound: no pair shared between jobs.
+  const i64 K1p = pair_k(K);
+  return (size_t)njobs * npairs * (al256((size_t)8 * M * K1p * 2) + al256((size_t)8 * N * K1p * 2));
 }
 
 int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream_t s) {
@@ -699,55 +709,90 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   for (int j = 1; j < g.njobs; ++j)
     if ((g.jobs[j].A2 != nullptr) != (npairs == 2))
       return fail(MPC_EINVAL, "limb engine: jobs mix one- and two-pair products");
-  const i64 Kp = padded_k(g.K, npairs);
+  const i64 K1p = pair_k(g.K);
   const size_t need = limb_workspace_bytes(g.M, g.N, g.K, npairs, g.njobs);
   if (ws == nullptr || ws_bytes < need)
     return fail(MPC_ENOMEM, "limb workspace %zu bytes, need %zu", ws_bytes, need);
   const i64 gy = ceil_div(g.M, BM), gx = ceil_div(g.N, BN);
   if (gy > 65535) return fail(MPC_EUNSUPPORTED, "M too large for the limb engine grid");
+  if (ceil_div(g.N, PB_TN) > 65535) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
   int* st = device_status_ptr();
   if (!st) return fail(MPC_ECUDA, "device status word unavailable");
 
-  // Planes for every job.
-  PlaneJobs ja = {}, jbv = {};
-  char* w = static_cast<char*>(ws);
+  // One plane buffer per distinct (side, pair, source); jobs that share a
+  // source share its buffer and tensor map.
   LimbParams prm;
   memset(&prm, 0, sizeof(prm));
+  char* w = static_cast<char*>(ws);
+  const size_t a_bytes = al256((size_t)8 * g.M * K1p * 2), b_bytes = al256((size_t)8 * g.N * K1p * 2);
+  PlaneJobs ja = {}, jbv = {};
+  int na = 0, nb = 0;
+  for (int pr = 0; pr < npairs; ++pr) {
+    for (int j = 0; j < g.njobs; ++j) {
+      const u64* src = pr ? g.jobs[j].A2 : g.jobs[j].A1;
+      int hit = -1;
+      for (int u = 0; u < na; ++u)
+        if (ja.j[u].X1 == src) hit = u;
+      if (hit < 0) {
+        ja.j[na] = PlaneJob{src, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+        w += a_bytes;
+        hit = na++;
+      }
+      if (int rc = encode_planes(&prm.tmA[pr][j], ja.j[hit].out, g.M, K1p, BM)) return rc;
+    }
+  }
+  if (g.gather) {
+    // pair 1: the opened gather, shared; pair 2 (two-pair products): one per job
+    nb = npairs == 2 ? 1 + g.njobs : 1;
+    for (int z = 0; z < nb; ++z) {
+      jbv.j[z] = PlaneJob{nullptr, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+      w += b_bytes;
+    }
+    for (int j = 0; j < g.njobs; ++j) {
+      if (int rc = encode_planes(&prm.tmB[0][j], jbv.j[0].out, g.N, K1p, BN)) return rc;
+      if (npairs == 2)
+        if (int rc = encode_planes(&prm.tmB[1][j], jbv.j[1 + j].out, g.N, K1p, BN)) return rc;
+    }
+  } else {
+    for (int pr = 0; pr < npairs; ++pr) {
+      for (int j = 0; j < g.njobs; ++j) {
+        const u64* src = pr ? g.jobs[j].B2 : g.jobs[j].B1;
+        int hit = -1;
+        for (int u = 0; u < nb; ++u)
+          if (jbv.j[u].X1 == src) hit = u;
+        if (hit < 0) {
+          jbv.j[nb] = PlaneJob{src, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+          w += b_bytes;
+          hit = nb++;
+        }
+        if (int rc = encode_planes(&prm.tmB[pr][j], jbv.j[hit].out, g.N, K1p, BN)) return rc;
+      }
+    }
+  }
   for (int j = 0; j < g.njobs; ++j) {
-    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al256((size_t)8 * g.M * Kp * 2);
-    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al256((size_t)8 * g.N * Kp * 2);
-    ja.j[j] = PlaneJob{g.jobs[j].A1, g.jobs[j].A2, pa};
-    jbv.j[j] = PlaneJob{g.jobs[j].B1, g.jobs[j].B2, pb};
-    if (int rc = encode_planes(&prm.tmA[j], pa, g.M, Kp, BM)) return rc;
-    if (int rc = encode_planes(&prm.tmB[j], pb, g.N, Kp, BN)) return rc;
     prm.C[j] = g.jobs[j].C;
     prm.Z[j] = g.jobs[j].Z;
   }
   {
     KernelTimer timer("limb_planes", s);
-    const i64 ta = g.M * (Kp / 8);
-    dim3 ga(grid_for(ta, 256, 148 * 16), g.njobs);
-    dim3 gb((unsigned)ceil_div(Kp, PB_TK), (unsigned)ceil_div(g.N, PB_TN), g.njobs);
-    if (ceil_div(g.N, PB_TN) > 65535) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
-    limb_planes_a<<<ga, 256, 0, s>>>(ja, g.M, g.K, Kp);
+    const i64 ta = g.M * (K1p / 8);
+    dim3 ga(grid_for(ta, 256, 148 * 16), na);
+    limb_planes_a<<<ga, 256, 0, s>>>(ja, g.M, g.K, K1p);
     if (int rc = check_launch("limb_planes_a")) return rc;
+    dim3 gb((unsigned)ceil_div(K1p, PB_TK), (unsigned)ceil_div(g.N, PB_TN), nb);
     if (g.gather) {
-      for (int j = 0; j < g.njobs; ++j) {
-        dim3 gj(gb.x, gb.y, 1);
-        limb_planes_b_conv<<<gj, 256, 0, s>>>(*g.gather, j, jbv.j[j].out, g.N, g.K, Kp);
-        if (int rc = check_launch("limb_planes_b_conv")) return rc;
-      }
+      limb_planes_b_conv<<<gb, 256, 0, s>>>(*g.gather, jbv, g.N, g.K, K1p);
+      if (int rc = check_launch("limb_planes_b_conv")) return rc;
     } else {
-      limb_planes_b<<<gb, 256, 0, s>>>(jbv, g.N, g.K, Kp);
+      limb_planes_b<<<gb, 256, 0, s>>>(jbv, g.N, g.K, K1p);
       if (int rc = check_launch("limb_planes_b")) return rc;
     }
   }
   prm.M = g.M;
   prm.N = g.N;
   prm.hw_out = g.hw_out;
-  prm.T = (int)(Kp / KS);
+  prm.T1 = (int)(K1p / KS);
+  prm.T = npairs * prm.T1;
   prm.trunc_bits = g.trunc_bits;
   prm.splits = g.splits;
   prm.njobs = g.njobs;
