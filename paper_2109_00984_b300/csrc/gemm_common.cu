@@ -1,4 +1,5 @@
 // Split-K planning and the reduction of partial sums shared by both engines.
+#include <algorithm>
 #include "gemm.hpp"
 #include "host.hpp"
 
@@ -23,19 +24,33 @@ int choose_splits(i64 tiles, i64 units, i64 min_units) {
 
 namespace {
 
+// Rows (job, row) on the y grid, columns on threads: coalesced partial reads,
+// one 32-bit division per element for the conv output scatter.
 __global__ void __launch_bounds__(256) gemm_reduce_kernel(const GemmArgs g) {
   const i64 MN = g.M * g.N;
-  const i64 total = MN * g.njobs;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
-       i += (i64)gridDim.x * blockDim.x) {
-    const int job = (int)(i / MN);
-    const i64 e = i % MN, row = e / g.N, col = e % g.N;
-    u64 v = 0;
-    for (int s = 0; s < g.splits; ++s) v += g.partial[((i64)s * g.njobs + job) * MN + e];
-    const i64 idx = gemm_out_index(row, col, g.M, g.N, g.hw_out);
-    if (g.jobs[job].C) v += g.jobs[job].C[idx];
-    if (g.trunc_bits > 0) v = sar(v, g.trunc_bits);
-    g.jobs[job].Z[idx] = v;
+  const i64 rows = g.M * g.njobs;
+  const uint32_t hw = (uint32_t)g.hw_out;
+  for (i64 rj = blockIdx.y; rj < rows; rj += gridDim.y) {
+    const int job = (int)(rj / g.M);
+    const i64 row = rj - (i64)job * g.M;
+    const u64* part = g.partial + (i64)job * MN + row * g.N;
+    const u64* C = g.jobs[job].C;
+    u64* Z = g.jobs[job].Z;
+    for (i64 col = blockIdx.x * (i64)blockDim.x + threadIdx.x; col < g.N;
+         col += (i64)gridDim.x * blockDim.x) {
+      u64 v = 0;
+      for (int s = 0; s < g.splits; ++s) v += part[(i64)s * g.njobs * MN + col];
+      i64 idx;
+      if (hw) {
+        const uint32_t b = (uint32_t)col / hw;
+        idx = ((i64)b * g.M + row) * hw + ((uint32_t)col - b * hw);
+      } else {
+        idx = row * g.N + col;
+      }
+      if (C) v += C[idx];
+      if (g.trunc_bits > 0) v = sar(v, g.trunc_bits);
+      Z[idx] = v;
+    }
   }
 }
 
@@ -44,7 +59,10 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(const GemmArgs g) {
 int gemm_reduce(const GemmArgs& g, cudaStream_t s) {
   const i64 total = g.M * g.N * g.njobs;
   if (total == 0) return MPC_OK;
-  gemm_reduce_kernel<<<grid_for(total, 256), 256, 0, s>>>(g);
+  const i64 rows = g.M * g.njobs;
+  const unsigned gx = (unsigned)std::min<i64>(ceil_div(g.N, 256), 64);
+  const unsigned gy = (unsigned)std::min<i64>(rows, 65535);
+  gemm_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(g);
   return check_launch("gemm_reduce");
 }
 

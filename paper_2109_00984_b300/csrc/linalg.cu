@@ -46,6 +46,19 @@ __global__ void __launch_bounds__(kThreads) fill_sum_kernel(int P, i64 n, u64 se
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
        t += (i64)gridDim.x * blockDim.x) {
     const i64 i0 = 4 * t;
+    if (P == 2) {  // both blocks independent (instruction-level parallelism), 16-byte stores
+      const u64x4 r0 = prg_block(seed, op_id, stream_word2(role, 0, 0), t);
+      const u64x4 r1 = prg_block(seed, op_id, stream_word2(role, 0, 1), t);
+      store4(Out, i0, n, as_quad(r0));
+      store4(Out + n, i0, n, as_quad(r1));
+      if (sum) {
+        Quad q;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q.v[j] = r0.v[j] + r1.v[j];
+        store4(sum, i0, n, q);
+      }
+      continue;
+    }
     u64 acc[4] = {0, 0, 0, 0};
     for (int p = 0; p < P; ++p) {
       const u64x4 r = prg_block(seed, op_id, stream_word2(role, 0, p), t);
