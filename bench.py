@@ -223,6 +223,18 @@ def run_ours(args):
         step(1000 + w, x_dev)
     torch.cuda.synchronize()
 
+    # Each timed step replays a CUDA graph of the whole forward (dealer, online
+    # phase and reveal on both streams) captured with that step's own schedule:
+    # one host call per step, every kernel re-run.  The launch count is taken
+    # from the library's counter while the timed steps are captured.
+    mpc.reset_stats()
+    graphs = net.capture(x_dev, [synth.speech_schedule(len(ws), step=i) for i in range(args.steps)])
+    stats = mpc.get_stats()
+    torch.cuda.synchronize()
+    for g, _ in graphs[:min(3, len(graphs))]:
+        g.replay()
+    torch.cuda.synchronize()
+
     # ---- device-timed region: K steps, L2 flushed between steps ----------
     # The headline pass runs uninstrumented; a second pass of the same K steps
     # with the library's per-launch events (they cost a few per cent) gives the
@@ -230,7 +242,6 @@ def run_ours(args):
     def timed_pass(first_step, profiled):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        mpc.reset_stats()
         mpc.profile_reset()
         mpc.profile_enable(profiled)
         if world > 1:
@@ -239,7 +250,10 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            step(first_step + i, x_dev)
+            if profiled:
+                step(first_step + i, x_dev)
+            else:
+                graphs[i][0].replay()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -252,7 +266,6 @@ def run_ours(args):
     time.sleep(0.5)
     step_ms = timed_pass(0, False)
     clk = clocks.stop()
-    stats = mpc.get_stats()
     prof_step_ms = timed_pass(args.steps, True)
     prof = {k: mpc.profile_read(k) for k in ("gemm_plain", "gemm_limb", "limb_planes",
                                                  "private_relu", "private_relu_fused")}
@@ -265,8 +278,11 @@ def run_ours(args):
     x_host = torch.from_numpy(x).pin_memory()
     out_host = torch.empty(tuple(net.out_real.shape), dtype=torch.float64).pin_memory()
     e2e_steps = max(3, args.steps // 2)
+    e2e_graphs = net.capture(x_dev, [synth.speech_schedule(len(ws), step=3000 + i)
+                                     for i in range(e2e_steps)])
     for w in range(2):
-        step(2000 + w, x_host.to(dev, non_blocking=True))
+        x_dev.copy_(x_host, non_blocking=True)
+        e2e_graphs[w % e2e_steps][0].replay()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -275,9 +291,10 @@ def run_ours(args):
     e_stop = torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
     for i in range(e2e_steps):
-        inp = x_host.to(dev, non_blocking=True)
-        out = step(3000 + i, inp)
-        out_host.copy_(out, non_blocking=True)
+        x_dev.copy_(x_host, non_blocking=True)     # this step's input, host -> device
+        g, out = e2e_graphs[i]
+        g.replay()
+        out_host.copy_(out, non_blocking=True)     # revealed output, device -> host
     e_stop.record(stream)
     torch.cuda.synchronize()
     e2e_s = job_time(max(time.perf_counter() - t0, e_start.elapsed_time(e_stop) / 1e3), world,

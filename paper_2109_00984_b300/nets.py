@@ -140,3 +140,25 @@ class PrivateConv1dStack:
         """Decoded float64 output, shape (batch, c_out, length)."""
         _, real = api.reveal(shares, self.frac_bits, ring=False, real=True)
         return real.view(self.out_real.shape)
+
+    def capture(self, x, schedules):
+        """Capture one CUDA graph per schedule of a whole private forward + reveal.
+
+        x is the (device) input buffer the graphs read; copy each batch into it
+        before replaying.  Every graph keeps its own op ids (fresh dealer
+        material per step); a replay re-runs every kernel of the step, dealer
+        included, on both streams, with one host call.  Returns a list of
+        (graph, revealed output) pairs.
+        """
+        out = []
+        main = torch.cuda.current_stream()
+        cs = torch.cuda.Stream(device=self.device)
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            for sched in schedules:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    y = self.reveal(self.forward(x, sched))
+                out.append((g, y))
+        main.wait_stream(cs)
+        return out
