@@ -71,3 +71,42 @@ def test_full_speech_stack_bit_exact(mpc, full_oracle, engine):
     assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
     assert nmse < 4e-4
+
+
+def _captured(mpc, x, ws, strides, pads, algo, schedules):
+    """Forward + reveal captured as CUDA graphs (the bench's timed path), replayed."""
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+    s0 = schedules[0]
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=algo,
+                             weight_ops=s0["weight_op"], seed=s0["seed"])
+    xd = dev_f64(x)
+    graphs = net.capture(xd, schedules)
+    results = []
+    for g, out in graphs:
+        g.replay()
+        torch.cuda.synchronize()
+        results.append((host(net.bufs[-1]["Y"]), out.cpu().numpy()))
+    return results
+
+
+def test_small_stack_graph_replay_bit_exact(mpc):
+    """Each replayed graph equals the oracle's forward for its own schedule."""
+    x, ws, strides, pads = synth.speech_small()
+    scheds = [synth.speech_schedule(len(ws), step=s) for s in (5, 6)]
+    for (got_shares, got_real), sched in zip(_captured(mpc, x, ws, strides, pads, mpc.AUTO, scheds),
+                                             scheds):
+        ref_real, ref_shares = _oracle(x, ws, strides, pads, sched)
+        assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
+        assert np.array_equal(got_real.reshape(ref_real.shape), ref_real)
+
+
+@pytest.mark.slow
+def test_full_speech_stack_graph_replay_bit_exact(mpc, full_oracle):
+    """The bench's timed path: graph replay of the full stack, limb engine, fused ReLU."""
+    x, ws, strides, pads = synth.speech_stack()
+    sched = synth.speech_schedule(len(ws))
+    (got_shares, got_real), = _captured(mpc, x, ws, strides, pads, mpc.AUTO, [sched])
+    ref_shares, plain = full_oracle
+    assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
+    nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
+    assert nmse < 4e-4
