@@ -221,3 +221,20 @@ class PrivateResNet18:
     def reveal(self, shares):
         _, real = api.reveal(shares, self.frac_bits, ring=False, real=True)
         return real
+
+    def capture(self, x, schedules):
+        """One CUDA graph per schedule of a whole private forward + reveal (both
+        streams, dealer included); x is the device input buffer the graphs read.
+        Returns a list of (graph, revealed logits) pairs."""
+        out = []
+        main = torch.cuda.current_stream()
+        cs = torch.cuda.Stream(device=self.device)
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            for sched in schedules:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    y = self.reveal(self.forward(x, sched))
+                out.append((g, y))
+        main.wait_stream(cs)
+        return out

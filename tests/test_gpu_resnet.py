@@ -102,3 +102,20 @@ def test_full_resnet_image0_bit_exact(mpc):
     plain = oresnet.plaintext_resnet18(x, W, synth.RESNET18)
     nmse = float(((got_real - plain) ** 2).sum() / (plain ** 2).sum())
     assert nmse < 4e-4
+
+
+def test_small_resnet_graph_replay_bit_exact(mpc):
+    """The bench's timed path: a captured forward + reveal, replayed, equals the oracle."""
+    from paper_2109_00984_b300.resnet import PrivateResNet18
+    x = synth.resnet_input(batch=2, hw=32)
+    sched = synth.resnet_schedule(step=4)
+    net = PrivateResNet18(synth.resnet_weights(), synth.RESNET18, sched, algo=mpc.AUTO)
+    xd = dev_f64(x)
+    net.reveal(net.forward(xd, synth.resnet_schedule(step=9)))   # warm-up sizes the workspaces
+    (g, out), = net.capture(xd, [sched])
+    g.replay()
+    torch.cuda.synchronize()
+    W = synth.resnet_weights()
+    Wsh = oresnet.share_resnet_weights(W, synth.RESNET18, sched)
+    ref_real, _ = oresnet.private_resnet18(x, Wsh, synth.RESNET18, sched, return_shares=True)
+    assert np.array_equal(out.cpu().numpy(), ref_real)
