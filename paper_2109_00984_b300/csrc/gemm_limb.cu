@@ -527,6 +527,25 @@ __global__ void __launch_bounds__(256) limb_planes_a(const __grid_constant__ Pla
 // distinct banks), then each warp writes 128-byte runs of one plane row.
 constexpr int PB_TK = 64, PB_TN = 32, PB_ROW = PB_TK / 2 + 1;  // words per smem row
 
+// Store phase of the B-side plane tiles: tile[plane][n][word] holds 64 k
+// (32 words of two bf16) for 32 columns n.  Each warp instruction writes four
+// rows of 128 bytes (16 bytes per lane) of one plane; Kp is a multiple of 16,
+// so every store is 16-byte aligned and k never straddles the end.
+__device__ __forceinline__ void store_b_tile(const uint32_t (*tile)[PB_TN][PB_ROW],
+                                             __nv_bfloat16* out, int N, int Kp, int n0, int k0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w4 = (lane & 7) * 4;  // first of this lane's four words
+  for (int idx = warp; idx < 8 * (PB_TN / 4); idx += 8) {
+    const int pl = idx / (PB_TN / 4), row = (idx % (PB_TN / 4)) * 4 + (lane >> 3);
+    const int nn = n0 + row, kk = k0 + 2 * w4;
+    if (nn < N && kk < Kp) {
+      const uint4 v = make_uint4(tile[pl][row][w4], tile[pl][row][w4 + 1], tile[pl][row][w4 + 2],
+                                 tile[pl][row][w4 + 3]);
+      *reinterpret_cast<uint4*>(out + ((size_t)pl * N + nn) * Kp + kk) = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ PlaneJobs js, i64 N,
                                                       i64 K, i64 Kp) {
   __shared__ uint32_t tile[8][PB_TN][PB_ROW];
@@ -554,15 +573,7 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
       tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
-  // Store phase: 8 planes x 32 rows; each warp writes whole 128-byte row runs.
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int r = warp; r < 8 * PB_TN; r += 8) {
-    const int pl = r / PB_TN, row = r % PB_TN;
-    const i64 nn = n0 + row;
-    const i64 kk = k0 + 2 * lane;
-    if (nn < N && kk < Kp)
-      *reinterpret_cast<uint32_t*>(jb.out + ((i64)pl * N + nn) * Kp + kk) = tile[pl][row][lane];
-  }
+  store_b_tile(tile, jb.out, (int)N, (int)Kp, (int)n0, (int)k0);
 }
 
 // B side of a convolution, gathered straight from the data (implicit im2col):
@@ -575,36 +586,38 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
 // thread, so an element costs two bounds checks and an add.
 __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant__ ConvGather cg,
                                                            const __grid_constant__ PlaneJobs outs,
-                                                           i64 N, i64 K, i64 Kp) {
+                                                           int N, int K, int Kp) {
   __shared__ uint32_t tile[8][PB_TN][PB_ROW];
-  __shared__ i64 tap_off[PB_TK];
-  __shared__ int tap_r[PB_TK], tap_s[PB_TK], tap_ok[PB_TK];
+  __shared__ int tap_off[PB_TK], tap_r[PB_TK], tap_s[PB_TK];
   const mpc_conv_desc& d = cg.d;
+  const int H = (int)d.h, W = (int)d.w;
   const int z = blockIdx.z;
   const u64* src2 = z > 0 ? cg.src2[z - 1] : nullptr;
   __nv_bfloat16* out = outs.j[z].out;
-  const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
+  const int k0 = blockIdx.x * PB_TK, n0 = blockIdx.y * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
   if (tid < PB_TK) {
-    const i64 k = k0 + tid;
-    if (k >= K) {
-      tap_ok[tid] = 0;
+    const int k = k0 + tid;
+    if (k >= K) {  // an out-of-range row offset makes every bounds check fail
       tap_off[tid] = 0;
-      tap_r[tid] = tap_s[tid] = 0;
+      tap_r[tid] = -(1 << 30);
+      tap_s[tid] = 0;
     } else {
-      const i64 s_ = k % d.kw, r = (k / d.kw) % d.kh, ci = k / (d.kw * d.kh);
-      tap_ok[tid] = 1;
-      tap_off[tid] = (ci * d.h + r) * d.w + s_;
-      tap_r[tid] = (int)r;
-      tap_s[tid] = (int)s_;
+      const int kw = (int)d.kw, kh = (int)d.kh;
+      const int s_ = k % kw, r = (k / kw) % kh, ci = k / (kw * kh);
+      tap_off[tid] = (ci * H + r) * W + s_;
+      tap_r[tid] = r;
+      tap_s[tid] = s_;
     }
   }
-  // Output column n -> (b, oh, ow), and the data offset of its window origin.
-  const i64 n = n0 + nl;
+  // Output column n -> (b, oh, ow), and the data offset of its window origin
+  // (32-bit: the host checks that every data offset fits).
+  const int n = n0 + nl;
   const bool n_ok = n < N;
-  const i64 ow = n % cg.wo, oh = (n / cg.wo) % cg.ho, b = n / (cg.wo * cg.ho);
-  const i64 oy = oh * d.stride_h - d.pad_h, ox = ow * d.stride_w - d.pad_w;
-  const i64 base = (b * d.c_in * d.h + oy) * d.w + ox;
+  const int wo = (int)cg.wo, ho = (int)cg.ho;
+  const int ow = n % wo, tq = n / wo, oh = tq % ho, b = tq / ho;
+  const int oy = oh * (int)d.stride_h - (int)d.pad_h, ox = ow * (int)d.stride_w - (int)d.pad_w;
+  const int base = (b * (int)d.c_in * H + oy) * W + ox;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -614,9 +627,9 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant_
     for (int e = 0; e < 2; ++e) {
       const int t = kl + e;
       v[e] = 0;
-      const i64 y = oy + tap_r[t], x = ox + tap_s[t];
-      if (n_ok && tap_ok[t] && y >= 0 && y < d.h && x >= 0 && x < d.w) {
-        const i64 off = base + tap_off[t];
+      const int y = oy + tap_r[t], x = ox + tap_s[t];
+      if (n_ok && (unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) {
+        const int off = base + tap_off[t];
         if (z == 0) {
           u64 acc = 0;
           for (int q = 0; q < cg.n1; ++q) {
@@ -635,14 +648,7 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant_
       tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int r = warp; r < 8 * PB_TN; r += 8) {
-    const int pl = r / PB_TN, row = r % PB_TN;
-    const i64 nn = n0 + row;
-    const i64 kk = k0 + 2 * lane;
-    if (nn < N && kk < Kp)
-      *reinterpret_cast<uint32_t*>(out + ((i64)pl * N + nn) * Kp + kk) = tile[pl][row][lane];
-  }
+  store_b_tile(tile, out, N, Kp, n0, k0);
 }
 
 // ---- host side -----------------------------------------------------------------------------
@@ -781,7 +787,12 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     if (int rc = check_launch("limb_planes_a")) return rc;
     dim3 gb((unsigned)ceil_div(K1p, PB_TK), (unsigned)ceil_div(g.N, PB_TN), nb);
     if (g.gather) {
-      limb_planes_b_conv<<<gb, 256, 0, s>>>(*g.gather, jbv, g.N, g.K, K1p);
+      const mpc_conv_desc& d = g.gather->d;
+      const i64 data = d.batch * d.c_in * d.h * d.w;
+      if (data >= (1ll << 31) || g.N >= (1ll << 31) || K1p >= (1ll << 31) ||
+          (i64)8 * g.N * K1p >= (1ll << 62))
+        return fail(MPC_EUNSUPPORTED, "convolution too large for the 32-bit gather");
+      limb_planes_b_conv<<<gb, 256, 0, s>>>(*g.gather, jbv, (int)g.N, (int)g.K, (int)K1p);
       if (int rc = check_launch("limb_planes_b_conv")) return rc;
     } else {
       limb_planes_b<<<gb, 256, 0, s>>>(jbv, g.N, g.K, K1p);
