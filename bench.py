@@ -33,6 +33,11 @@ WORKLOAD = ("speech-shaped private conv stack: 2 parties, batch 1, input 80x1600
             "Conv1d 80->256 k11 s2 + 6x Conv1d 256->256 k7 (pad k//2), each Beaver conv + "
             "truncation 2^16 + private ReLU (A2B/Kogge-Stone/B2A), Z/2^64, dealer in the step")
 L2_FLUSH_BYTES = 256 << 20
+# DRAM traffic of the limb GEMM per launch, averaged over the 14 launches of one
+# speech step (7 dealer GEMMs of one operand pair, 7 online GEMMs of two pairs
+# for two parties), from an ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum on the current kernel.
+LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 60.9e6
 REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
 
 
@@ -337,7 +342,10 @@ def run_ours(args):
     elif kern == "gemm_limb":
         achieved = 36 * 2 * macs * args.steps / (kms / 1e3) / 1e12   # limb-pair MMA flops
         roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": bf16_peak,
-                "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / bf16_peak,
+                "traffic": LIMB_GEMM_DRAM_BYTES_PER_LAUNCH,
+                "traffic_note": "bytes per launch, mean of the 14 limb GEMM launches of one "
+                                "step (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
                 "peak_source": peak_src + " (bf16 sustained)",
                 "launches_per_step": launches / args.steps,
                 "busy_ms_per_step": kms / args.steps,
