@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) ltz_kernel(i64 n, const u64* X, u64*
   }
 }
 
-__global__ void __launch_bounds__(256) relu_fused_quad_kernel(i64 n, const u64* X, u64* Y,
+__global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u64* X, u64* Y,
                                                               u64 seed, u64 op) {
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
