@@ -228,16 +228,21 @@ def run_ours(args):
         step(1000 + w, x_dev)
     torch.cuda.synchronize()
 
-    # Each timed step replays a CUDA graph of the whole forward (dealer, online
-    # phase and reveal on both streams) captured with that step's own schedule:
-    # one host call per step, every kernel re-run.  The launch count is taken
-    # from the library's counter while the timed steps are captured.
+    # Each timed step replays a CUDA graph captured with that step's own
+    # schedule (one host call per step, every kernel re-run).  The steps are
+    # software-pipelined as an MPC offline phase runs: step i runs the online
+    # phase of batch i on the triples dealt during step i - 1 while its dealer
+    # deals the triples of batch i + 1 on the other stream -- one forward's
+    # dealing and one forward's online phase per step.  The launch count is
+    # taken from the library's counter while the timed steps are captured.
+    scheds = [synth.speech_schedule(len(ws), step=i) for i in range(args.steps + 1)]
     mpc.reset_stats()
-    graphs = net.capture(x_dev, [synth.speech_schedule(len(ws), step=i) for i in range(args.steps)])
+    graphs = net.capture_pipelined(x_dev, scheds[:-1], scheds[1:])
     stats = mpc.get_stats()
-    torch.cuda.synchronize()
-    for g, _ in graphs[:min(3, len(graphs))]:
+    net.deal(scheds[0], 0, join=True)
+    for g, _ in graphs:          # first launches upload the graphs (untimed)
         g.replay()
+    net.deal(scheds[0], 0, join=True)   # step 0's triples again: replays consume their own
     torch.cuda.synchronize()
 
     # ---- device-timed region: K steps, L2 flushed between steps ----------
@@ -283,11 +288,13 @@ def run_ours(args):
     x_host = torch.from_numpy(x).pin_memory()
     out_host = torch.empty(tuple(net.out_real.shape), dtype=torch.float64).pin_memory()
     e2e_steps = max(3, args.steps // 2)
-    e2e_graphs = net.capture(x_dev, [synth.speech_schedule(len(ws), step=3000 + i)
-                                     for i in range(e2e_steps)])
-    for w in range(2):
+    e2e_scheds = [synth.speech_schedule(len(ws), step=3000 + i) for i in range(e2e_steps + 3)]
+    e2e_all = net.capture_pipelined(x_dev, e2e_scheds[:-1], e2e_scheds[1:])
+    net.deal(e2e_scheds[0], 0, join=True)
+    for w in range(2):           # untimed: upload and warm the first two steps
         x_dev.copy_(x_host, non_blocking=True)
-        e2e_graphs[w % e2e_steps][0].replay()
+        e2e_all[w][0].replay()
+    e2e_graphs = e2e_all[2:]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()

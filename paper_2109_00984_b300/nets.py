@@ -58,9 +58,6 @@ class PrivateConv1dStack:
             ho, wo = api.conv_out_hw(d)
             n = d.batch * d.c_out * ho * wo
             b = dict(
-                A=torch.empty((P, d.batch, d.c_in, d.h, d.w), dtype=torch.int64, device=dev),
-                B=torch.empty((P, d.c_out, d.c_in, d.kh, d.kw), dtype=torch.int64, device=dev),
-                C=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
                 Z=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
                 Y=torch.empty((P, d.batch, d.c_out, ho, wo), dtype=torch.int64, device=dev),
                 n=n,
@@ -73,6 +70,14 @@ class PrivateConv1dStack:
                          rb=torch.empty((P, (n + 63) // 64), dtype=torch.int64, device=dev),
                          MT=torch.empty((3, P, n), dtype=torch.int64, device=dev))
             self.bufs.append(b)
+        # Two slots of convolution triples, so that the dealer can fill one while
+        # the online phase consumes the other (forward_pipelined).
+        self.trip = [[dict(
+            A=torch.empty((P, d.batch, d.c_in, d.h, d.w), dtype=torch.int64, device=dev),
+            B=torch.empty((P, d.c_out, d.c_in, d.kh, d.kw), dtype=torch.int64, device=dev),
+            C=torch.empty((P, d.batch, d.c_out) + tuple(api.conv_out_hw(d)), dtype=torch.int64,
+                          device=dev)) for d in self.descs] for _ in range(2)]
+        self.ready = [[None] * len(self.descs) for _ in range(2)]
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         self.dealer_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         # The online phase is the critical path: it runs on a high-priority stream,
@@ -84,42 +89,84 @@ class PrivateConv1dStack:
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
                                     dtype=torch.float64, device=dev)
 
-    def forward(self, x, schedule):
-        """x: float64 CUDA tensor of the input shape. Returns output shares [P, ...]."""
+    def deal(self, schedule, slot=0, join=False):
+        """Enqueue the dealer's convolution triples of every layer for `schedule`
+        into triple slot `slot`, on the dealer stream (recording one event per
+        layer) when the dealer overlaps, else on the current stream.  With join
+        the current stream then waits for the dealer (use it when dealing ahead
+        of graph replays, which do not wait on these events)."""
         seed = schedule["seed"]
         main = torch.cuda.current_stream()
-        ready = []
-        if self.overlap_dealer:
-            ds = self.dealer_stream
+        ds = self.dealer_stream if self.overlap_dealer else main
+        if ds is not main:
             ds.wait_stream(main)
-            with torch.cuda.stream(ds):
-                for l, (d, b) in enumerate(zip(self.descs, self.bufs)):
-                    api.ttp_conv2d_triple(self.P, d, seed, schedule["layers"][l]["conv"], self.algo,
-                                          out=(b["A"], b["B"], b["C"]), ws=self.dealer_ws)
+        with torch.cuda.stream(ds):
+            for l, d in enumerate(self.descs):
+                t = self.trip[slot][l]
+                api.ttp_conv2d_triple(self.P, d, seed, schedule["layers"][l]["conv"], self.algo,
+                                      out=(t["A"], t["B"], t["C"]),
+                                      ws=self.dealer_ws if ds is not main else self.ws)
+                if ds is not main:
                     ev = torch.cuda.Event()
                     ev.record(ds)
-                    ready.append(ev)
-        if self.overlap_dealer:
-            on = self.online_stream
-            on.wait_stream(main)
-            with torch.cuda.stream(on):
-                X = self._online(x, schedule, on, ready)
-            main.wait_stream(on)
-            return X
-        return self._online(x, schedule, main, ready)
+                    self.ready[slot][l] = ev
+        if join and ds is not main:
+            main.wait_stream(ds)
 
-    def _online(self, x, schedule, main, ready):
+    def online(self, x, schedule, slot=0, wait_dealer=True):
+        """Online phase on the triples in `slot`: share the input, then per layer
+        the Beaver convolution (truncation fused) and the private ReLU.  With
+        wait_dealer each layer waits on the event its triple recorded."""
+        main = torch.cuda.current_stream()
+        if not self.overlap_dealer:
+            return self._online(x, schedule, slot, main, False)
+        on = self.online_stream
+        on.wait_stream(main)
+        with torch.cuda.stream(on):
+            X = self._online(x, schedule, slot, on, wait_dealer)
+        main.wait_stream(on)
+        return X
+
+    def _join_dealer(self):
+        if self.overlap_dealer:
+            torch.cuda.current_stream().wait_stream(self.dealer_stream)
+
+    def forward(self, x, schedule):
+        """x: float64 CUDA tensor of the input shape. Returns output shares [P, ...].
+
+        Deals this forward's triples and runs its online phase; with
+        overlap_dealer the dealer runs ahead on its own stream."""
+        if not self.overlap_dealer:
+            return self._online(x, schedule, 0, torch.cuda.current_stream(), False, deal=True)
+        self.deal(schedule, 0)
+        X = self.online(x, schedule, 0)
+        self._join_dealer()
+        return X
+
+    def forward_pipelined(self, x, schedule, slot, next_schedule, wait_dealer=True):
+        """One step of a software-pipelined sequence: the online phase of
+        `schedule` on the triples already dealt into `slot` (by the previous
+        step, or by deal() before the first), while the dealer deals
+        `next_schedule` into the other slot.  Every step still deals one forward's
+        triples and runs one forward's online phase."""
+        self.deal(next_schedule, 1 - slot)
+        X = self.online(x, schedule, slot, wait_dealer)
+        self._join_dealer()
+        return X
+
+    def _online(self, x, schedule, slot, main, wait_dealer, deal=False):
         seed = schedule["seed"]
         api.ring_share(x, self.P, 0, seed, schedule["input_op"], self.frac_bits, out=self.X0)
         X = self.X0
         for l, (d, b) in enumerate(zip(self.descs, self.bufs)):
             ops = schedule["layers"][l]
-            if self.overlap_dealer:
-                main.wait_event(ready[l])
-            else:
+            t = self.trip[slot][l]
+            if deal:
                 api.ttp_conv2d_triple(self.P, d, seed, ops["conv"], self.algo,
-                                      out=(b["A"], b["B"], b["C"]), ws=self.ws)
-            api.beaver_conv2d(X, self.W[l], b["A"], b["B"], b["C"], d, self.algo,
+                                      out=(t["A"], t["B"], t["C"]), ws=self.ws)
+            elif wait_dealer and self.ready[slot][l] is not None:
+                main.wait_event(self.ready[slot][l])
+            api.beaver_conv2d(X, self.W[l], t["A"], t["B"], t["C"], d, self.algo,
                               trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)
             n = b["n"]
             if self.fused_relu:
@@ -159,6 +206,27 @@ class PrivateConv1dStack:
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=cs):
                     y = self.reveal(self.forward(x, sched))
+                out.append((g, y))
+        main.wait_stream(cs)
+        return out
+
+    def capture_pipelined(self, x, schedules, next_schedules):
+        """One CUDA graph per step of a software-pipelined sequence: graph i runs
+        the online phase of schedules[i] on triple slot i % 2 and deals
+        next_schedules[i] into the other slot.  Replay the graphs in order, after
+        deal(schedules[0], 0, join=True); stream order between replays orders each step's
+        online phase after the dealing of the step before.  Returns a list of
+        (graph, revealed output) pairs."""
+        out = []
+        main = torch.cuda.current_stream()
+        cs = torch.cuda.Stream(device=self.device)
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            for i, (sched, nxt) in enumerate(zip(schedules, next_schedules)):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    y = self.reveal(self.forward_pipelined(x, sched, i % 2, nxt,
+                                                           wait_dealer=False))
                 out.append((g, y))
         main.wait_stream(cs)
         return out

@@ -110,3 +110,30 @@ def test_full_speech_stack_graph_replay_bit_exact(mpc, full_oracle):
     assert np.array_equal(got_shares.reshape(ref_shares.shape), ref_shares)
     nmse = float(((got_real.reshape(plain.shape) - plain) ** 2).sum() / (plain ** 2).sum())
     assert nmse < 4e-4
+
+
+def test_small_stack_pipelined_bit_exact(mpc):
+    """Software-pipelined steps (online phase of batch i on the triples dealt
+    during step i - 1), as graph replays and eagerly: every output equals the
+    oracle's forward for its own schedule."""
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+    x, ws, strides, pads = synth.speech_small()
+    scheds = [synth.speech_schedule(len(ws), step=s) for s in (11, 12, 13, 14)]
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=mpc.AUTO,
+                             weight_ops=scheds[0]["weight_op"], seed=scheds[0]["seed"])
+    xd = dev_f64(x)
+    refs = [_oracle(x, ws, strides, pads, s) for s in scheds[:3]]
+    graphs = net.capture_pipelined(xd, scheds[:3], scheds[1:])
+    net.deal(scheds[0], 0, join=True)
+    for (g, out), (ref_real, ref_shares) in zip(graphs, refs):
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(net.bufs[-1]["Y"]).reshape(ref_shares.shape), ref_shares)
+        assert np.array_equal(out.cpu().numpy().reshape(ref_real.shape), ref_real)
+    net.deal(scheds[0], 0)     # eager steps wait on the dealer's events instead
+    for i, (ref_real, ref_shares) in enumerate(refs):
+        Y = net.forward_pipelined(xd, scheds[i], i % 2, scheds[i + 1])
+        real = net.reveal(Y)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(Y).reshape(ref_shares.shape), ref_shares)
+        assert np.array_equal(real.cpu().numpy().reshape(ref_real.shape), ref_real)
