@@ -18,11 +18,13 @@
 //    128 x 128 x 16 MACs, which the tensor core's shared-memory port sustains at
 //    full rate (N = 64 with eight accumulators would read 6 KiB per half the
 //    work and cap the tensor pipe near two thirds of its peak);
-//  * |d_i d_j| <= 2^14 and at most 8 pairs share a shift, so 128 K-steps keep
+//  * |d_i d_j| <= 2^14 and shift s sums s + 1 pairs, so 64 / (s + 1)
+//    sub-steps of K = 16 (1024 K-steps for shift 0, 128 for shift 7) keep
 //    every partial sum within 2^24 where fp32 holds integers exactly.  Each
-//    accumulator is therefore drained every 8 sub-steps of K = 16 (chunks
-//    staggered by accumulator, one drain every other sub-step) into a 64-bit
-//    integer register sum R += int(acc_s) << 8s;
+//    accumulator is drained at the end of such a chunk (chunks staggered by
+//    slot) into a 64-bit integer register sum R += int(acc_s) << 8s: 0.58
+//    drains per sub-step over both passes, where a common chunk of 8 for
+//    every shift would take one;
 //  * the epilogue adds C, applies the optional truncation and stores.
 //
 // Operands arrive as planes written by limb_planes_{a,b}: A as [8][M][Kp]
@@ -52,7 +54,7 @@ namespace mpc {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, KS = 16, STAGES = 3, NPLANE = 8, NSLOT = 4, CHUNK = 8;
+constexpr int BM = 128, BN = 128, KS = 16, STAGES = 3, NPLANE = 8, NSLOT = 4;
 constexpr int PLANE_BYTES = BM * KS * 2;               // 4 KiB: one digit plane of a tile
 constexpr int A_STAGE_BYTES = NPLANE * PLANE_BYTES;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_STAGE_BYTES;         // A then B planes: 64 KiB
@@ -205,11 +207,19 @@ __device__ __forceinline__ void issue_shift(uint32_t d, uint64_t a0, uint64_t b0
            b0 + (uint64_t)((s - i) * (PLANE_BYTES >> 4)), 1u);
 }
 
-// The chunk of accumulator slot q ends after sub-step t when t = 2q + 1
-// (mod 8), or at the end t_end - 1 of the K range: one drain every other
-// sub-step.
-__device__ __forceinline__ bool chunk_ends(int t, int q, int t_end) {
-  return (t & (CHUNK - 1)) == 2 * q + 1 || t == t_end - 1;
+// Chunk length of shift s in sub-steps of K = 16: the shift sums the s + 1
+// digit pairs (i, s - i), each product at most 2^14 in magnitude, so
+// L_s = 64 / (s + 1) sub-steps keep every partial sum within
+// L_s * 16 * (s + 1) * 2^14 <= 2^24 (64, 32, 21, 16, 12, 10, 9, 8).
+__device__ __forceinline__ int chunk_len(int s) { return 64 / (s + 1); }
+
+// Sub-steps left, t included, in the chunk of shift s (slot s % 4) that holds
+// sub-step t: a chunk ends when (t + s % 4 * L_s / 4) % L_s = L_s - 1, which
+// staggers the four slots' drains by a quarter period.  The last sub-step of
+// the K range ends every chunk.
+__device__ __forceinline__ int chunk_left(int t, int s) {
+  const int L = chunk_len(s);
+  return L - (t + (s & 3) * L / 4) % L;
 }
 
 // TMA loads of sub-step g (over both passes): pass 0 digit planes 0..3 of A and
@@ -273,6 +283,8 @@ __device__ __forceinline__ void issuer_loop(int q, uint32_t sbase, uint32_t tmem
       if (!ld->load(gl)) return;
   uint32_t chunks = 0;
   const uint32_t d = tmem + (uint32_t)(q * BN);
+  int left = 0;
+  bool start = true;
   for (int g = 0; g < total; ++g) {
     if (ld && gl < total) {
       if (!ld->load(gl)) return;
@@ -281,21 +293,26 @@ __device__ __forceinline__ void issuer_loop(int q, uint32_t sbase, uint32_t tmem
     const int pass = g >= steps;
     const int t = t_begin + g - pass * steps;
     const int shift = 4 * pass + q;
+    if (t == t_begin) {
+      left = chunk_left(t, shift);
+      start = true;
+    }
     const int st = g % STAGES;
     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
     if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
     tc_fence_after();
     const uint64_t a0 = smem_desc_sw32(sbase + st * STAGE_BYTES);
     const uint64_t b0 = smem_desc_sw32(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
-    const bool start = (t == t_begin) || chunk_ends(t - 1, q, t_end);
     if (start && chunks > 0) {
       if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return;
       tc_fence_after();
     }
     issue_shift(d, a0, b0, shift, start);
-    if (chunk_ends(t, q, t_end)) {
+    start = --left == 0 || t == t_end - 1;
+    if (start) {
       tc_commit(&accf_bar[q]);
       chunks++;
+      left = chunk_len(shift);
     }
     tc_commit(&empty_bar[st]);
   }
@@ -404,16 +421,19 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
       return true;
     };
     for (int pass = 0; pass < 2 && ok; ++pass) {
-      for (int t = t_begin; t < t_end && ok; ++t) {
-        if (t < t_end - 1) {
-          if (t & 1) {
-            const int q = (t & (CHUNK - 1)) >> 1;  // t = 2q + 1 (mod 8)
-            ok = drain(q, 8 * (4 * pass + q));
-          }
-        } else {
+      // Byte q: sub-steps left in slot q's chunk (1..64), all four decremented
+      // together; a byte that reaches 0 is refilled with the chunk length.
+      uint32_t left = 0;
 #pragma unroll
-          for (int q = 0; q < NSLOT; ++q)
+      for (int q = 0; q < NSLOT; ++q) left |= (uint32_t)chunk_left(t_begin, 4 * pass + q) << (8 * q);
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        left -= 0x01010101u;
+#pragma unroll
+        for (int q = 0; q < NSLOT; ++q) {
+          if (((left >> (8 * q)) & 0xFFu) == 0u || t == t_end - 1) {
             if (ok) ok = drain(q, 8 * (4 * pass + q));
+            left |= (uint32_t)chunk_len(4 * pass + q) << (8 * q);
+          }
         }
       }
     }

@@ -2,9 +2,9 @@
 
 The limb engine cuts each word into 8 balanced base-256 digits held exactly in
 bf16, accumulates the 36 digit pairs with i + j < 8 in fp32 tensor memory and
-drains every 128 K-steps so no partial sum leaves the range where fp32 is
-exact.  The adversarial case below drives every digit to -128, so each full
-chunk of the top shift sums to exactly 2^24, the edge of exactness.
+drains shift s every 1024 / (s + 1) K-steps so no partial sum leaves the range
+where fp32 is exact.  The adversarial cases below drive every digit to -128,
+so each full chunk sums to exactly 2^24, the edge of exactness.
 """
 import numpy as np
 import pytest
@@ -65,6 +65,24 @@ def test_ring_gemm_limb_exactness_edge(mpc, K):
     a2 = np.full((M, K), M64, dtype=np.uint64)
     Z2 = mpc.ring_gemm(dev(a2), dev(b), None, algo=mpc.LIMB)
     assert np.array_equal(host(Z2), _gemm_ref(a2, b))
+
+
+def test_ring_gemm_limb_exactness_full_chunks(mpc, rng):
+    """148 tiles and K = 2096 run unsplit, so every shift s reaches a full chunk of
+    64 / (s + 1) sub-steps of K = 16; with all digits -128 each sums to 2^24.
+    Constant rows of A make every entry a closed form: Z[i, j] = a * sum_k B[k, j]."""
+    M, N, K = 512, 37 * 128, 2096
+    a = np.full((M, K), ALL_MINUS_128, dtype=np.uint64)
+    b = np.full((K, N), ALL_MINUS_128, dtype=np.uint64)
+    Z = host(mpc.ring_gemm(dev(a), dev(b), None, algo=mpc.LIMB))
+    mpc.sync_status()
+    assert np.all(Z == np.uint64(K * ALL_MINUS_128 * ALL_MINUS_128 & M64))
+    b = u64(rng, (K, N))
+    b[:, :7] = ALL_MINUS_128
+    Z = host(mpc.ring_gemm(dev(a), dev(b), None, algo=mpc.LIMB))
+    with np.errstate(over="ignore"):
+        col = b.sum(axis=0, dtype=np.uint64) * np.uint64(ALL_MINUS_128)
+    assert np.array_equal(Z, np.broadcast_to(col, (M, N)))
 
 
 def test_ring_gemm_limb_mixed_extremes(mpc, rng):
