@@ -27,9 +27,17 @@
 //    every shift would take one;
 //  * the epilogue adds C, applies the optional truncation and stores.
 //
-// Operands arrive as planes written by limb_planes_{a,b}: A as [8][M][Kp]
-// and B transposed as [8][N][Kp] (both K-major), with K-concatenated operand
-// pairs (Z = C + A1 B1 + A2 B2 is one GEMM over [A1 | A2] and [B1 ; B2]).
+// Operands arrive as digit planes written by limb_planes_{a,b}: A by rows of
+// M, B transposed by rows of N (both K-major), interleaved per sub-step: row r
+// holds, for each sub-step t of 16 k, the 16 digits of planes 0..7 in turn
+// (256 contiguous bytes), i.e. [rows][T][8][16] bf16.  A TMA box is 128 rows x
+// 128 bytes (planes 0..3 or 4..7 of one sub-step) with the 128-byte swizzle,
+// so the copy engine fetches whole 128-byte lines (a [8][rows][K] layout with
+// 32-byte boxes made four times as many L2 requests, which capped the tensor
+// pipe near 78 %); the MMA of plane p starts 32 (p % 4) bytes into the
+// swizzled rows, as a K-step inside a 128-byte swizzle atom would.
+// K-concatenated operand pairs (Z = C + A1 B1 + A2 B2) are one GEMM over
+// [A1 | A2] and [B1 ; B2], each pair with its own planes.
 //
 // Warp roles (640 threads): warps 0-3 each issue the MMAs of one accumulator
 // slot q (shift q in pass 0, 4 + q in pass 1), one thread per warp; that
@@ -58,7 +66,7 @@ constexpr int BM = 128, BN = 128, KS = 16, STAGES = 3, NPLANE = 8, NSLOT = 4;
 constexpr int PLANE_BYTES = BM * KS * 2;               // 4 KiB: one digit plane of a tile
 constexpr int A_STAGE_BYTES = NPLANE * PLANE_BYTES;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_STAGE_BYTES;         // A then B planes: 64 KiB
-constexpr int HALF_LOAD_BYTES = 4 * PLANE_BYTES;       // one TMA box: 4 planes
+constexpr int HALF_LOAD_BYTES = 4 * PLANE_BYTES;       // one TMA box: 128 rows x 128 B
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int kIssuers = 4;      // MMA-issuing warps (0..3); warp 0 also loads
 constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps (4..19)
@@ -73,8 +81,8 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
                            ((uint32_t)(BM >> 4) << 24);
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
-// Each operand pair has its own planes ([8][rows][K1p], K1p = K rounded up to
-// 16), so a pair that all jobs share (the opened E or F) is cut into digits
+// Each operand pair has its own planes ([rows][K1p / 16][8][16], K1p = K
+// rounded up to 16), so a pair that all jobs share (the opened E or F) is cut into digits
 // once: tmA[pair][job] / tmB[pair][job] of different jobs may map one buffer.
 struct LimbParams {
   CUtensorMap tmA[2][MPC_MAX_PARTIES];
@@ -144,12 +152,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
-                                            int x, int y, int z) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
 
@@ -174,15 +182,22 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
 }
 
-// Shared-memory matrix descriptor: K-major, 32-byte swizzle, rows of 32 bytes,
-// 8-row groups 256 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
   d |= (uint64_t)1 << 46;                    // version
-  d |= (uint64_t)6 << 61;                    // SWIZZLE_32B
+  d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
   return d;
+}
+
+// Descriptor offset (16-byte units) of digit plane p inside a stage region:
+// planes 0..3 in the first 128 x 128-byte box, 4..7 in the second, plane p
+// starting 32 (p % 4) bytes into each swizzled row.
+__device__ __forceinline__ uint64_t plane_desc_off(int p) {
+  return (uint64_t)(((p >> 2) * HALF_LOAD_BYTES + (p & 3) * 32) >> 4);
 }
 
 #define TMEM_LD_X16(taddr, r)                                                                  \
@@ -201,10 +216,8 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // The s + 1 digit-pair MMAs of shift s: D += sum_{i <= s} A_i B_{s - i}.
 __device__ __forceinline__ void issue_shift(uint32_t d, uint64_t a0, uint64_t b0, int s,
                                             bool start) {
-  tc_mma(d, a0, b0 + (uint64_t)(s * (PLANE_BYTES >> 4)), start ? 0u : 1u);
-  for (int i = 1; i <= s; ++i)
-    tc_mma(d, a0 + (uint64_t)(i * (PLANE_BYTES >> 4)),
-           b0 + (uint64_t)((s - i) * (PLANE_BYTES >> 4)), 1u);
+  tc_mma(d, a0, b0 + plane_desc_off(s), start ? 0u : 1u);
+  for (int i = 1; i <= s; ++i) tc_mma(d, a0 + plane_desc_off(i), b0 + plane_desc_off(s - i), 1u);
 }
 
 // Chunk length of shift s in sub-steps of K = 16: the shift sums the s + 1
@@ -235,7 +248,7 @@ struct Loader {
     const int pass = g >= steps;
     const int t = t_begin + g - pass * steps;
     const int pair = t >= p->T1;
-    const int x = (t - pair * p->T1) * KS;
+    const int tl = t - pair * p->T1;
     const CUtensorMap* ta = &p->tmA[pair][job];
     const CUtensorMap* tb = &p->tmB[pair][job];
     const int st = g % STAGES;
@@ -244,11 +257,11 @@ struct Loader {
     mbar_arrive_expect_tx(&full_bar[st], (pass ? 4 : 2) * HALF_LOAD_BYTES);
     const uint32_t a_dst = sbase + st * STAGE_BYTES;
     const uint32_t b_dst = a_dst + A_STAGE_BYTES;
-    tma_load_3d(a_dst, ta, &full_bar[st], x, m0, 0);
-    tma_load_3d(b_dst, tb, &full_bar[st], x, n0, 0);
+    tma_load_4d(a_dst, ta, &full_bar[st], 0, 0, tl, m0);
+    tma_load_4d(b_dst, tb, &full_bar[st], 0, 0, tl, n0);
     if (pass) {
-      tma_load_3d(a_dst + HALF_LOAD_BYTES, ta, &full_bar[st], x, m0, 4);
-      tma_load_3d(b_dst + HALF_LOAD_BYTES, tb, &full_bar[st], x, n0, 4);
+      tma_load_4d(a_dst + HALF_LOAD_BYTES, ta, &full_bar[st], 0, 1, tl, m0);
+      tma_load_4d(b_dst + HALF_LOAD_BYTES, tb, &full_bar[st], 0, 1, tl, n0);
     }
     last_g[st] = g;
     return true;
@@ -301,8 +314,8 @@ __device__ __forceinline__ void issuer_loop(int q, uint32_t sbase, uint32_t tmem
     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
     if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
     tc_fence_after();
-    const uint64_t a0 = smem_desc_sw32(sbase + st * STAGE_BYTES);
-    const uint64_t b0 = smem_desc_sw32(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
+    const uint64_t a0 = smem_desc_sw128(sbase + st * STAGE_BYTES);
+    const uint64_t b0 = smem_desc_sw128(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
     if (start && chunks > 0) {
       if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return;
       tc_fence_after();
@@ -495,9 +508,16 @@ __device__ __forceinline__ uint32_t pack_hi16(uint32_t lo_bits, uint32_t hi_bits
   return __byte_perm(lo_bits, hi_bits, 0x7632u);
 }
 
-// Writes 8 consecutive k' of one row into the 8 planes of `out` ([8][rows][Kp]).
-__device__ __forceinline__ void write_planes(const u64 v[8], __nv_bfloat16* out, i64 rows,
-                                             i64 row, i64 Kp, i64 k0) {
+// Element offset of digit (plane p, row, k) in interleaved planes
+// [rows][Kp / 16][8][16] (Kp a multiple of 16).
+__device__ __forceinline__ i64 plane_index(int p, i64 row, i64 Kp, i64 k) {
+  return ((row * (Kp / KS) + k / KS) * NPLANE + p) * KS + (k % KS);
+}
+
+// Writes 8 consecutive k' (k0 a multiple of 8) of one row into its 8 digit
+// planes: eight 16-byte stores, 32 bytes apart.
+__device__ __forceinline__ void write_planes(const u64 v[8], __nv_bfloat16* out, i64 row, i64 Kp,
+                                             i64 k0) {
   u64 u[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) u[e] = digit_base(v[e]);
@@ -508,7 +528,7 @@ __device__ __forceinline__ void write_planes(const u64 v[8], __nv_bfloat16* out,
     w.y = pack_hi16(digit_bits(u[2], pl), digit_bits(u[3], pl));
     w.z = pack_hi16(digit_bits(u[4], pl), digit_bits(u[5], pl));
     w.w = pack_hi16(digit_bits(u[6], pl), digit_bits(u[7], pl));
-    *reinterpret_cast<uint4*>(out + ((i64)pl * rows + row) * Kp + k0) = w;
+    *reinterpret_cast<uint4*>(out + plane_index(pl, row, Kp, k0)) = w;
   }
 }
 
@@ -537,38 +557,49 @@ __global__ void __launch_bounds__(256) limb_planes_a(const __grid_constant__ Pla
       const i64 k = k0 + e;
       v[e] = k < K ? jb.X1[m * K + k] : (jb.X2 && k < 2 * K) ? jb.X2[m * K + (k - K)] : 0ull;
     }
-    write_planes(v, jb.out, M, m, Kp, k0);
+    write_planes(v, jb.out, m, Kp, k0);
   }
 }
 
-// B side: X is [K][N] row-major; planes are written transposed, [8][N][Kp].
+// B side: X is [K][N] row-major; planes are written transposed, by rows of N.
 // One CTA per tile of 64 k' x 32 n: coalesced row reads of X, digits into a
 // shared-memory tile [plane][n][k'] (33-word rows: the transposed stores hit
-// distinct banks), then each warp writes 128-byte runs of one plane row.
+// distinct banks), then each warp instruction writes 512 contiguous bytes of
+// one row's interleaved planes.
 constexpr int PB_TK = 64, PB_TN = 32, PB_ROW = PB_TK / 2 + 1;  // words per smem row
+constexpr int PB_PLANE = PB_TN * PB_ROW;                       // words per tile plane
+constexpr int PB_WORDS = NPLANE * PB_PLANE + 20;
 
-// Store phase of the B-side plane tiles: tile[plane][n][word] holds 64 k
-// (32 words of two bf16) for 32 columns n.  Each warp instruction writes four
-// rows of 128 bytes (16 bytes per lane) of one plane; Kp is a multiple of 16,
-// so every store is 16-byte aligned and k never straddles the end.
-__device__ __forceinline__ void store_b_tile(const uint32_t (*tile)[PB_TN][PB_ROW],
-                                             __nv_bfloat16* out, int N, int Kp, int n0, int k0) {
+// Word index of (plane p, column n, word w) in the tile.  Plane p is skewed by
+// (p % 4) + 16 (p / 4) words so that the store phase, whose lanes read planes
+// 0..7 at word offsets {0, 4, 8, 12}, touches 32 distinct banks.
+__device__ __forceinline__ int pb_word(int p, int n, int w) {
+  return p * PB_PLANE + (p & 3) + 16 * (p >> 2) + n * PB_ROW + w;
+}
+
+// Store phase of the B-side plane tiles: the tile holds 64 k (32 words of two
+// bf16), i.e. four sub-steps, for 32 columns n; in the interleaved layout
+// those are 1024 contiguous bytes per column.  Lane l of a warp instruction
+// writes 16 bytes: sub-step (l / 16) + 2 h, plane (l / 2) % 8, k half l % 2.
+// Kp is a multiple of 16, so a sub-step never straddles the end.
+__device__ __forceinline__ void store_b_tile(const uint32_t* tile, __nv_bfloat16* out, int N,
+                                             int Kp, int n0, int k0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w4 = (lane & 7) * 4;  // first of this lane's four words
-  for (int idx = warp; idx < 8 * (PB_TN / 4); idx += 8) {
-    const int pl = idx / (PB_TN / 4), row = (idx % (PB_TN / 4)) * 4 + (lane >> 3);
-    const int nn = n0 + row, kk = k0 + 2 * w4;
+  const int pl = (lane >> 1) & 7, half = lane & 1;
+  for (int idx = warp; idx < 2 * PB_TN; idx += 8) {
+    const int row = idx >> 1, tl = (lane >> 4) + 2 * (idx & 1);
+    const int nn = n0 + row, kk = k0 + KS * tl;
     if (nn < N && kk < Kp) {
-      const uint4 v = make_uint4(tile[pl][row][w4], tile[pl][row][w4 + 1], tile[pl][row][w4 + 2],
-                                 tile[pl][row][w4 + 3]);
-      *reinterpret_cast<uint4*>(out + ((size_t)pl * N + nn) * Kp + kk) = v;
+      const int w4 = pb_word(pl, row, 8 * tl + 4 * half);
+      const uint4 v = make_uint4(tile[w4], tile[w4 + 1], tile[w4 + 2], tile[w4 + 3]);
+      *reinterpret_cast<uint4*>(out + plane_index(pl, nn, Kp, kk + 8 * half)) = v;
     }
   }
 }
 
 __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ PlaneJobs js, i64 N,
                                                       i64 K, i64 Kp) {
-  __shared__ uint32_t tile[8][PB_TN][PB_ROW];
+  __shared__ uint32_t tile[PB_WORDS];
   const PlaneJob& jb = js.j[blockIdx.z];
   const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
@@ -590,7 +621,7 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
     const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
 #pragma unroll
     for (int pl = 0; pl < 8; ++pl)
-      tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
   store_b_tile(tile, jb.out, (int)N, (int)Kp, (int)n0, (int)k0);
@@ -607,7 +638,7 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
 __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant__ ConvGather cg,
                                                            const __grid_constant__ PlaneJobs outs,
                                                            int N, int K, int Kp) {
-  __shared__ uint32_t tile[8][PB_TN][PB_ROW];
+  __shared__ uint32_t tile[PB_WORDS];
   __shared__ int tap_off[PB_TK], tap_r[PB_TK], tap_s[PB_TK];
   const mpc_conv_desc& d = cg.d;
   const int H = (int)d.h, W = (int)d.w;
@@ -665,7 +696,7 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant_
     const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
 #pragma unroll
     for (int pl = 0; pl < 8; ++pl)
-      tile[pl][nl][kl >> 1] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
   }
   __syncthreads();
   store_b_tile(tile, out, N, Kp, n0, k0);
@@ -687,15 +718,17 @@ int get_encoder() {
   return g_encode ? MPC_OK : fail(MPC_ECUDA, "cuTensorMapEncodeTiled unavailable");
 }
 
-// 3-D map over planes [8][rows][Kp] bf16 with a {16, box_rows, 4} box, 32-byte swizzle.
+// 4-D map over interleaved planes [rows][Kp / 16][2][64] bf16 (the last two
+// dims: planes 0..3 | 4..7 of a sub-step, 4 x 16 digits each) with a box of
+// {64, 1, 1, box_rows}: 128 rows of 128 bytes, 128-byte swizzle.
 int encode_planes(CUtensorMap* tm, const void* base, i64 rows, i64 Kp, int box_rows) {
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 8};
-  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 4};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+  cuuint64_t dims[4] = {64, 2, (cuuint64_t)(Kp / KS), (cuuint64_t)rows};
+  cuuint64_t strides[3] = {128, 256, (cuuint64_t)(Kp / KS) * 256};
+  cuuint32_t box[4] = {64, 1, 1, (cuuint32_t)box_rows};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? MPC_OK : fail(MPC_ECUDA, "tensor map encode failed (%d)", (int)r);
 }
