@@ -413,23 +413,40 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
     uint32_t parity = 0;  // bit q: parity of the next chunk of slot q
     bool ok = true;
     // Drain slot q's finished chunk of shift sh / 8 into R.
-    auto drain = [&](int q, int sh) -> bool {
-      if (!mbar_wait(&accf_bar[q], (parity >> q) & 1u, &abort_flag)) return false;
-      tc_fence_after();
+    // R[j] += int(acc) << sh for 16 columns.  From shift 4 on (sh >= 32) only
+    // the upper word changes: one 32-bit shift-add per value.
+    auto accumulate = [&](const uint32_t (&v)[16], u64* Rh, int sh) {
+      if (sh >= 32) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {  // two loads of 16 columns: 80 live registers, not 96
-        uint32_t v[16];
-        TMEM_LD_X16(lane_base + (uint32_t)(q * BN + 16 * h), v);
-        tmem_wait_ld();
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t iv = (uint32_t)__float2int_rz(__uint_as_float(v[j]));
+          const uint32_t hi = (uint32_t)(Rh[j] >> 32) + (iv << (sh - 32));
+          Rh[j] = (Rh[j] & 0xFFFFFFFFull) | ((u64)hi << 32);
+        }
+      } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int iv = __float2int_rz(__uint_as_float(v[j]));
-          R[16 * h + j] += (u64)(i64)iv << sh;
+          Rh[j] += (u64)(i64)iv << sh;
         }
       }
+    };
+    // Drain slot q's finished chunk of shift sh / 8 into R.  The slot is
+    // released to its issuer as soon as both 16-column loads have landed, so
+    // the second half's conversion overlaps the next chunk's MMAs.
+    auto drain = [&](int q, int sh) -> bool {
+      if (!mbar_wait(&accf_bar[q], (parity >> q) & 1u, &abort_flag)) return false;
+      tc_fence_after();
+      uint32_t v[16];  // one 16-column load at a time: 80 live registers, not 96
+      TMEM_LD_X16(lane_base + (uint32_t)(q * BN), v);
+      tmem_wait_ld();
+      accumulate(v, R, sh);
+      TMEM_LD_X16(lane_base + (uint32_t)(q * BN + 16), v);
+      tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar[q]);
+      accumulate(v, R + 16, sh);
       parity ^= 1u << q;
       return true;
     };
