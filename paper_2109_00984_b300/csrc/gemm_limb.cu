@@ -75,6 +75,7 @@ constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps (4..19)
 constexpr int kThreads = 32 * (kIssuers + kDrainWarps);
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(BM == BN, "A and B plane tiles share one layout");
+static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "epilogue tile fits the stages");
 // Instruction descriptor, kind::f16: D f32 (bit 4), A bf16 (bits 7-9 = 1),
 // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -467,26 +468,45 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
         }
       }
     }
-    const i64 row = (i64)m0 + quad * 32 + lane;
-    const int c0 = n0 + cblk * 32;
-    if (ok && !abort_flag && row < p.M) {
-      if (p.splits > 1) {
-        u64* part = p.partial + ((i64)split * p.njobs + job) * p.M * p.N + row * p.N;
+    // Epilogue through shared memory (the operand stages are idle once every
+    // chunk is drained): each thread parks its 32 sums of one row, then each
+    // warp writes whole rows, 256 contiguous bytes per store instruction,
+    // instead of 32 rows x 8 bytes.  Rows of 129 words keep the parking
+    // stores at the two wavefronts that 256 bytes need.
+    constexpr int SROW = BN + 1;
+    u64* stile = reinterpret_cast<u64*>(dsmem + (sbase - smem_u32(dsmem)));
+    if (ok && !abort_flag) {
+      u64* mine = stile + (quad * 32 + lane) * SROW + cblk * 32;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if ((i64)c0 + j < p.N) part[c0 + j] = R[j];
-      } else {
-        const u64* C = p.C[job];
-        u64* Z = p.Z[job];
+      for (int j = 0; j < 32; ++j) mine[j] = R[j];
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kDrainWarps) : "memory");
+    if (!abort_flag) {
+      for (int r = ew; r < BM; r += kDrainWarps) {
+        const i64 row = (i64)m0 + r;
+        if (row >= p.M) break;
+        const u64* src = stile + r * SROW;
+        if (p.splits > 1) {
+          u64* part = p.partial + ((i64)split * p.njobs + job) * p.M * p.N + row * p.N;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const i64 col = (i64)c0 + j;
-          if (col < p.N) {
-            const i64 idx = gemm_out_index(row, col, p.M, p.N, p.hw_out);
-            u64 v = R[j];
-            if (C) v += C[idx];
-            if (p.trunc_bits > 0) v = sar(v, p.trunc_bits);
-            Z[idx] = v;
+          for (int k = 0; k < BN / 32; ++k) {
+            const int c = 32 * k + lane;
+            if ((i64)n0 + c < p.N) part[n0 + c] = src[c];
+          }
+        } else {
+          const u64* C = p.C[job];
+          u64* Z = p.Z[job];
+#pragma unroll
+          for (int k = 0; k < BN / 32; ++k) {
+            const int c = 32 * k + lane;
+            const i64 col = (i64)n0 + c;
+            if (col < p.N) {
+              const i64 idx = gemm_out_index(row, col, p.M, p.N, p.hw_out);
+              u64 v = src[c];
+              if (C) v += C[idx];
+              if (p.trunc_bits > 0) v = sar(v, p.trunc_bits);
+              Z[idx] = v;
+            }
           }
         }
       }
