@@ -27,7 +27,7 @@
 //    every shift would take one;
 //  * the epilogue adds C, applies the optional truncation and stores.
 //
-// Operands arrive as digit planes written by limb_planes_{a,b}: A by rows of
+// Operands arrive as digit planes written by limb_planes: A by rows of
 // M, B transposed by rows of N (both K-major), interleaved per sub-step: row r
 // holds, for each sub-step t of 16 k, the 16 digits of planes 0..7 in turn
 // (256 contiguous bytes), i.e. [rows][T][8][16] bf16.  A TMA box is 128 rows x
@@ -53,6 +53,7 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gemm.hpp"
@@ -579,14 +580,13 @@ struct PlaneJobs {
   PlaneJob j[2 * MPC_MAX_PARTIES];
 };
 
-// A side: X is [M][K] row-major; element (m, k') of [X1 | X2].
-__global__ void __launch_bounds__(256) limb_planes_a(const __grid_constant__ PlaneJobs js, i64 M,
-                                                      i64 K, i64 Kp) {
-  const PlaneJob& jb = js.j[blockIdx.y];
+// A side: X is [M][K] row-major; element (m, k') of [X1 | X2].  Block `blk`
+// of `nblk` strides over job jb's 8-k groups.
+__device__ __forceinline__ void planes_a_part(const PlaneJob& jb, i64 M, i64 K, i64 Kp, i64 blk,
+                                              i64 nblk) {
   const i64 kc = Kp / 8;
   const i64 total = M * kc;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
-       i += (i64)gridDim.x * blockDim.x) {
+  for (i64 i = blk * (i64)blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
     const i64 m = i / kc, k0 = (i % kc) * 8;
     u64 v[8];
 #pragma unroll
@@ -634,11 +634,9 @@ __device__ __forceinline__ void store_b_tile(const uint32_t* tile, __nv_bfloat16
   }
 }
 
-__global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ PlaneJobs js, i64 N,
-                                                      i64 K, i64 Kp) {
-  __shared__ uint32_t tile[PB_WORDS];
-  const PlaneJob& jb = js.j[blockIdx.z];
-  const i64 k0 = (i64)blockIdx.x * PB_TK, n0 = (i64)blockIdx.y * PB_TN;
+__device__ __forceinline__ void planes_b_tile(uint32_t* tile, const PlaneJob& jb, i64 N, i64 K,
+                                              i64 Kp, int bx, int by) {
+  const i64 k0 = (i64)bx * PB_TK, n0 = (i64)by * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
   const i64 n = n0 + nl;
   // Load + digit phase: thread (nl, kq) owns k' pairs 2 (kq + 8 j), j = 0..3.
@@ -665,24 +663,21 @@ __global__ void __launch_bounds__(256) limb_planes_b(const __grid_constant__ Pla
 }
 
 // B side of a convolution, gathered straight from the data (implicit im2col):
-// the same tiling and stores as limb_planes_b, with element (k, n) read at its
-// data position instead of from a materialised im2col matrix.  blockIdx.z = 0
-// writes pair 1 (the opened sum over src1 - sub1, shared by all jobs) to
-// outs.j[0].out; blockIdx.z = 1 + j writes job j's pair 2 (src2[j]) to
-// outs.j[1 + j].out.  The CTA's 64 k are decoded once into a shared tap table
+// the same tiling and stores as planes_b_tile, with element (k, n) read at its
+// data position instead of from a materialised im2col matrix.  z = 0 writes
+// pair 1 (the opened sum over src1 - sub1, shared by all jobs) to
+// outs.j[0].out; z = 1 + j writes job j's pair 2 (src2[j]) to outs.j[1 + j].out.  The CTA's 64 k are decoded once into a shared tap table
 // (offset ci h w + r w + s, r, s); column n = (b, oh, ow) is decoded once per
 // thread, so an element costs two bounds checks and an add.
-__global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant__ ConvGather cg,
-                                                           const __grid_constant__ PlaneJobs outs,
-                                                           int N, int K, int Kp) {
-  __shared__ uint32_t tile[PB_WORDS];
-  __shared__ int tap_off[PB_TK], tap_r[PB_TK], tap_s[PB_TK];
+__device__ __forceinline__ void planes_b_conv_tile(uint32_t* tile, int* tap_off, int* tap_r,
+                                                   int* tap_s, const ConvGather& cg,
+                                                   const PlaneJobs& outs, int N, int K, int Kp,
+                                                   int bx, int by, int z) {
   const mpc_conv_desc& d = cg.d;
   const int H = (int)d.h, W = (int)d.w;
-  const int z = blockIdx.z;
   const u64* src2 = z > 0 ? cg.src2[z - 1] : nullptr;
   __nv_bfloat16* out = outs.j[z].out;
-  const int k0 = blockIdx.x * PB_TK, n0 = blockIdx.y * PB_TN;
+  const int k0 = bx * PB_TK, n0 = by * PB_TN;
   const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
   if (tid < PB_TK) {
     const int k = k0 + tid;
@@ -737,6 +732,36 @@ __global__ void __launch_bounds__(256) limb_planes_b_conv(const __grid_constant_
   }
   __syncthreads();
   store_b_tile(tile, out, N, Kp, n0, k0);
+}
+
+// One launch for both plane sides of a GEMM: blocks [0, na * a_blk) cut the A
+// sources (a_blk blocks per job), the rest the B tiles (bx x by per source,
+// nb sources), the B side either from row-major X or, with GATHER, from the
+// convolution data.  Saves a kernel boundary per GEMM.
+struct PlanesLaunch {
+  PlaneJobs ja, jb;
+  ConvGather cg;
+  i64 M, N, K, Kp;
+  int na, a_blk, nb, bx, by;
+};
+
+template <bool GATHER>
+__global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ PlanesLaunch pl) {
+  __shared__ uint32_t tile[PB_WORDS];
+  __shared__ int tap_off[PB_TK], tap_r[PB_TK], tap_s[PB_TK];
+  const i64 b = blockIdx.x;
+  const i64 a_blocks = (i64)pl.na * pl.a_blk;
+  if (b < a_blocks) {
+    planes_a_part(pl.ja.j[b / pl.a_blk], pl.M, pl.K, pl.Kp, b % pl.a_blk, pl.a_blk);
+    return;
+  }
+  const int r = (int)(b - a_blocks);
+  const int bx = r % pl.bx, by = (r / pl.bx) % pl.by, z = r / (pl.bx * pl.by);
+  if (GATHER)
+    planes_b_conv_tile(tile, tap_off, tap_r, tap_s, pl.cg, pl.jb, (int)pl.N, (int)pl.K,
+                       (int)pl.Kp, bx, by, z);
+  else
+    planes_b_tile(tile, pl.jb.j[z], pl.N, pl.K, pl.Kp, bx, by);
 }
 
 // ---- host side -----------------------------------------------------------------------------
@@ -871,23 +896,34 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   }
   {
     KernelTimer timer("limb_planes", s);
-    const i64 ta = g.M * (K1p / 8);
-    dim3 ga(grid_for(ta, 256, 148 * 16), na);
-    limb_planes_a<<<ga, 256, 0, s>>>(ja, g.M, g.K, K1p);
-    if (int rc = check_launch("limb_planes_a")) return rc;
-    dim3 gb((unsigned)ceil_div(K1p, PB_TK), (unsigned)ceil_div(g.N, PB_TN), nb);
+    PlanesLaunch pl;
+    memset(&pl, 0, sizeof(pl));
+    pl.ja = ja;
+    pl.jb = jbv;
+    pl.M = g.M;
+    pl.N = g.N;
+    pl.K = g.K;
+    pl.Kp = K1p;
+    pl.na = na;
+    pl.nb = nb;
+    pl.bx = (int)ceil_div(K1p, PB_TK);
+    pl.by = (int)ceil_div(g.N, PB_TN);
+    // A side: about as many threads as 8-k groups, at most 4 blocks per SM and job.
+    pl.a_blk = (int)std::min<i64>(ceil_div(g.M * (K1p / 8), 256), 148 * 4);
+    const i64 blocks = (i64)na * pl.a_blk + (i64)nb * pl.bx * pl.by;
+    if (blocks > 0x7FFFFFFFll) return fail(MPC_EUNSUPPORTED, "plane pass grid too large");
     if (g.gather) {
       const mpc_conv_desc& d = g.gather->d;
       const i64 data = d.batch * d.c_in * d.h * d.w;
       if (data >= (1ll << 31) || g.N >= (1ll << 31) || K1p >= (1ll << 31) ||
           (i64)8 * g.N * K1p >= (1ll << 62))
         return fail(MPC_EUNSUPPORTED, "convolution too large for the 32-bit gather");
-      limb_planes_b_conv<<<gb, 256, 0, s>>>(*g.gather, jbv, (int)g.N, (int)g.K, (int)K1p);
-      if (int rc = check_launch("limb_planes_b_conv")) return rc;
+      pl.cg = *g.gather;
+      limb_planes<true><<<(unsigned)blocks, 256, 0, s>>>(pl);
     } else {
-      limb_planes_b<<<gb, 256, 0, s>>>(jbv, g.N, g.K, K1p);
-      if (int rc = check_launch("limb_planes_b")) return rc;
+      limb_planes<false><<<(unsigned)blocks, 256, 0, s>>>(pl);
     }
+    if (int rc = check_launch("limb_planes")) return rc;
   }
   prm.M = g.M;
   prm.N = g.N;
