@@ -74,6 +74,13 @@ constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps (4..19)
 // 20 warps, 5 per SM sub-partition: up to 96 registers per thread (the drain
 // warps hold 32 64-bit sums each).
 constexpr int kThreads = 32 * (kIssuers + kDrainWarps);
+// Register split after launch (setmaxnreg): the issuing warpgroup keeps 56 per
+// thread, the drain warpgroups take 104, enough to hold a slot's 32 drained
+// columns beside the 32 64-bit sums.
+constexpr int kLaunchRegs = 96, kIssuerRegs = 56, kDrainRegs = 104;
+static_assert(kIssuers == 4 && kDrainWarps % 4 == 0, "warpgroup-aligned roles");
+static_assert(32 * kIssuers * kIssuerRegs + 32 * kDrainWarps * kDrainRegs <= kThreads * kLaunchRegs,
+              "register split exceeds the launch allocation");
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(BM == BN, "A and B plane tiles share one layout");
 static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "epilogue tile fits the stages");
@@ -380,6 +387,9 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   const int steps = t_end - t_begin;
 
   if (warp < kIssuers) {
+    // The issuing warpgroup hands registers to the drain warpgroups:
+    // 128 x 56 + 512 x 104 = 60 416 <= 640 x 96 launched.
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssuerRegs));
     if (lane == 0) {
       // ---- MMA issuers: warp q owns accumulator slot q; warp 0 also loads ----
       Loader ldr;
@@ -405,6 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
     }
   } else {
     // ---- TMEM drain + epilogue: 16 warps, four per TMEM lane quadrant ----
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs));
     const int ew = warp - kIssuers;               // 0..15
     const int quad = warp & 3;                    // lane quadrant this warp may access
     const int cblk = ew >> 2;                     // which 32 of the 128 columns
@@ -435,20 +446,20 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
     };
     // Drain slot q's finished chunk of shift sh / 8 into R.  The slot is
     // released to its issuer as soon as both 16-column loads have landed, so
-    // the second half's conversion overlaps the next chunk's MMAs.
+    // the conversions overlap the next chunk's MMAs (the 32 loaded columns
+    // beside R need the drain warps' larger register share).
     auto drain = [&](int q, int sh) -> bool {
       if (!mbar_wait(&accf_bar[q], (parity >> q) & 1u, &abort_flag)) return false;
       tc_fence_after();
-      uint32_t v[16];  // one 16-column load at a time: 80 live registers, not 96
+      uint32_t v[16], w[16];
       TMEM_LD_X16(lane_base + (uint32_t)(q * BN), v);
-      tmem_wait_ld();
-      accumulate(v, R, sh);
-      TMEM_LD_X16(lane_base + (uint32_t)(q * BN + 16), v);
+      TMEM_LD_X16(lane_base + (uint32_t)(q * BN + 16), w);
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar[q]);
-      accumulate(v, R + 16, sh);
+      accumulate(v, R, sh);
+      accumulate(w, R + 16, sh);
       parity ^= 1u << q;
       return true;
     };
