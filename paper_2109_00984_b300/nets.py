@@ -215,8 +215,11 @@ class PrivateConv1dStack:
         the online phase of schedules[i] on triple slot i % 2 and deals
         next_schedules[i] into the other slot.  Replay the graphs in order, after
         deal(schedules[0], 0, join=True); stream order between replays orders each step's
-        online phase after the dealing of the step before.  Returns a list of
-        (graph, revealed output) pairs."""
+        online phase after the dealing of the step before.  x is the input buffer
+        the graphs read, or a list of buffers (graph i reads x[i % len(x)], so
+        that the next step's input can be uploaded while a step runs).  Returns a
+        list of (graph, revealed output) pairs."""
+        xs = x if isinstance(x, (list, tuple)) else [x]
         out = []
         main = torch.cuda.current_stream()
         cs = torch.cuda.Stream(device=self.device)
@@ -225,7 +228,7 @@ class PrivateConv1dStack:
             for i, (sched, nxt) in enumerate(zip(schedules, next_schedules)):
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=cs):
-                    y = self.reveal(self.forward_pipelined(x, sched, i % 2, nxt,
+                    y = self.reveal(self.forward_pipelined(xs[i % len(xs)], sched, i % 2, nxt,
                                                            wait_dealer=False))
                 out.append((g, y))
         main.wait_stream(cs)
