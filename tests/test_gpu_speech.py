@@ -137,3 +137,25 @@ def test_small_stack_pipelined_bit_exact(mpc):
         torch.cuda.synchronize()
         assert np.array_equal(host(Y).reshape(ref_shares.shape), ref_shares)
         assert np.array_equal(real.cpu().numpy().reshape(ref_real.shape), ref_real)
+
+
+def test_small_stack_pipelined_two_input_buffers(mpc):
+    """Pipelined graphs reading alternating input buffers (graph i reads
+    buffer i % 2, so the next input can be uploaded while a step runs): each
+    step's output equals the oracle's forward on that step's own input."""
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+    x, ws, strides, pads = synth.speech_small()
+    x2 = x[..., ::-1].copy()   # a second, different input of the same shape
+    scheds = [synth.speech_schedule(len(ws), step=s) for s in (21, 22, 23, 24)]
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=mpc.AUTO,
+                             weight_ops=scheds[0]["weight_op"], seed=scheds[0]["seed"])
+    inputs = [x, x2, x]
+    bufs = [dev_f64(x), dev_f64(x2)]
+    refs = [_oracle(inp, ws, strides, pads, s) for inp, s in zip(inputs, scheds[:3])]
+    graphs = net.capture_pipelined(bufs, scheds[:3], scheds[1:])
+    net.deal(scheds[0], 0, join=True)
+    for (g, out), (ref_real, ref_shares) in zip(graphs, refs):
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(net.bufs[-1]["Y"]).reshape(ref_shares.shape), ref_shares)
+        assert np.array_equal(out.cpu().numpy().reshape(ref_real.shape), ref_real)
