@@ -25,7 +25,9 @@
 //    slot) into a 64-bit integer register sum R += int(acc_s) << 8s: 0.58
 //    drains per sub-step over both passes, where a common chunk of 8 for
 //    every shift would take one;
-//  * the epilogue adds C, applies the optional truncation and stores.
+//  * the epilogue parks the sums in shared memory (the operand stages are idle
+//    by then) and writes whole rows: it adds C, applies the optional
+//    truncation and stores, or stores the split-K partial.
 //
 // Operands arrive as digit planes written by limb_planes: A by rows of
 // M, B transposed by rows of N (both K-major), interleaved per sub-step: row r
@@ -33,9 +35,9 @@
 // (256 contiguous bytes), i.e. [rows][T][8][16] bf16.  A TMA box is 128 rows x
 // 128 bytes (planes 0..3 or 4..7 of one sub-step) with the 128-byte swizzle,
 // so the copy engine fetches whole 128-byte lines (a [8][rows][K] layout with
-// 32-byte boxes made four times as many L2 requests, which capped the tensor
-// pipe near 78 %); the MMA of plane p starts 32 (p % 4) bytes into the
-// swizzled rows, as a K-step inside a 128-byte swizzle atom would.
+// 32-byte boxes made four times as many L2 requests); the MMA of plane p
+// starts 32 (p % 4) bytes into the swizzled rows, as a K-step inside a
+// 128-byte swizzle atom would.
 // K-concatenated operand pairs (Z = C + A1 B1 + A2 B2) are one GEMM over
 // [A1 | A2] and [B1 ; B2], each pair with its own planes.
 //
@@ -44,7 +46,10 @@
 // thread of warp 0 also issues the TMA loads, STAGES - 1 sub-steps ahead of
 // its own MMAs; warp 0 allocates TMEM; warps 4-19 drain TMEM, four per lane
 // quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each, and write
-// the output.  Every wait is bounded: on a timeout the CTA records
+// the output.  After launch (96 registers per thread) the issuing warpgroup
+// drops to 56 and the drain warpgroups rise to 104 (setmaxnreg), so a drain
+// can hold a slot's 32 loaded columns beside its 32 64-bit sums and release
+// the slot before converting.  Every wait is bounded: on a timeout the CTA records
 // MPC_ETIMEOUT, waits (bounded) for its own copies and MMAs, frees TMEM and
 // returns.
 #include <cuda.h>
