@@ -132,3 +132,48 @@ def test_approx_rejects_other_party_counts(mpc):
     X = dev(np.zeros((3, 8), np.uint64))
     with pytest.raises(mpc.MPCError):
         mpc.exp(X, SEED, 1)
+
+
+BENCH_N = 1 << 25   # the element count the approximation bench times
+
+
+@pytest.mark.parametrize("fn", ["exp", "sigmoid", "reciprocal_pos", "log"])
+def test_full_size_properties(mpc, fn):
+    """At the bench's size (2^25 elements, same launch shapes), the revealed
+    outputs stay within the closed-form error bounds the oracle is pinned to
+    (EXP_REL = 0.019 for the limit exponential and what inherits from it)."""
+    EXP_REL, ULP = 0.019, 2.0 ** -16
+    g = torch.Generator(device="cuda").manual_seed(7)
+    lo, hi, is_log = {"exp": (-4.0, 2.0, False), "sigmoid": (-8.0, 8.0, False),
+                      "reciprocal_pos": (0.1, 20.0, True), "log": (0.01, 100.0, True)}[fn]
+    if is_log:
+        u = torch.rand(BENCH_N, generator=g, device="cuda", dtype=torch.float64)
+        x = torch.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+    else:
+        x = lo + (hi - lo) * torch.rand(BENCH_N, generator=g, device="cuda", dtype=torch.float64)
+    X = mpc.ring_share(x, 2, 0, SEED, 31)
+    if fn == "exp":
+        Y = mpc.exp(X, SEED, 40000)
+    elif fn == "sigmoid":
+        Y = mpc.sigmoid(X, SEED, 40000)
+    elif fn == "reciprocal_pos":
+        Y = mpc.reciprocal(X, SEED, 40000, all_positive=True)
+    else:
+        Y = mpc.log(X, SEED, 40000)
+    mpc.sync_status()
+    _, y = mpc.reveal(Y, 16)
+    xe = x.double()
+    if fn == "exp":
+        ref = (1 + xe / 256) ** 256
+        bad = (y / ref - 1).abs() >= EXP_REL
+    elif fn == "sigmoid":
+        bad = (y - torch.sigmoid(xe)).abs() >= EXP_REL / 4 + 2e-3
+    elif fn == "reciprocal_pos":
+        bad = (y - 1 / xe).abs() > 2e-3 * (1 / xe).abs() + 8 * ULP
+    else:
+        ystar = 256 * (1 - xe ** (-1 / 256))
+        bad = (y - ystar).abs() >= EXP_REL
+    # A two-party local truncation wraps with probability about |v| / 2^64
+    # (v <= 2^24 here), i.e. well under one element in 2^25 over all the
+    # truncations of a function: allow at most two.
+    assert int(bad.sum()) <= 2
