@@ -61,7 +61,7 @@ typedef enum {
   MPC_ENOMEM = -3,      /* caller-provided workspace too small               */
   MPC_ECUDA = -4,       /* a CUDA runtime call or kernel launch failed       */
   MPC_ETIMEOUT = -5,    /* a bounded device-side wait gave up                */
-  MPC_EUNSUPPORTED = -6 /* valid request this build does not implement       */
+  MPC_EUNSUPPORTED = -6 /* valid request the library does not implement      */
 } mpc_status;
 
 /* Ring GEMM engines for matmul / conv. */
