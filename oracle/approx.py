@@ -23,7 +23,7 @@ Readings (the paper fixes the methods, not every constant or order):
     built by repeated products with x^2;
   * inverse square root: y <- y (3 - x y^2) / 2 (the /2 folded into the last
     product's truncation, by 17 bits), 10 iterations.  The paper gives no
-    initial value; the oracle (and the kernels) use y0 = 3 g^16 + 0.3 g + 0.05 with
+    initial value; the oracle uses y0 = 3 g^16 + 0.3 g + 0.05 with
     g = exp(-x / 16) (g^16 = exp(-x) by four more squarings), which keeps
     y0 sqrt(x) within (0.3, 1.6), inside the convergence interval (0, sqrt 3),
     for x in [0.01, 100]; sqrt(x) = x * x^(-1/2);
