@@ -39,7 +39,10 @@
  *    bounded wait that gave up) are recorded in a per-device status word and
  *    returned by the next mpc_sync_status().
  *  - Parties: 1 <= P <= MPC_MAX_PARTIES.  The binary-share calls (mpc_a2b,
- *    mpc_private_relu) support P = 2 only (one carry-lookahead adder).
+ *    mpc_private_relu, mpc_ltz) need P >= 2: for P = 2 the two binary-shared
+ *    words go through one carry-lookahead adder, for P = 3..8 through a tree
+ *    of ceil(log2 P) adder levels (P - 1 adders).  The fused-dealer calls
+ *    (mpc_private_relu_fused and the function approximations) take P = 2 only.
  */
 #ifndef MPC_RING_H
 #define MPC_RING_H
@@ -140,6 +143,18 @@ int mpc_profile_read(const char* kernel, uint64_t* launches, double* total_ms);
  * once, so work / busy time is the kernel's throughput while it runs. */
 int mpc_profile_busy(const char* kernel, double* busy_ms);
 
+/* Diagnostic of the bounded-wait status path (the paper has no counterpart:
+ * it concerns this library's device-side failure reporting).  Launches one
+ * warp on `stream` whose thread 0 waits for an mbarrier phase that never
+ * completes, through the same bounded wait and abort flag the limb engine's
+ * roles use, but with a limit of limit_ns (1 us .. 1 s) instead of 2 s.  When
+ * the limit passes it records MPC_ETIMEOUT in the device status word and the
+ * kernel returns; nothing else is in flight, so the context stays usable.  The
+ * next mpc_sync_status() returns MPC_ETIMEOUT (and clears it).  A limb-engine
+ * launch made while the status word still holds MPC_ETIMEOUT gives up at its
+ * first wait that does not complete at once, so read the status first. */
+int mpc_test_wait_timeout(int64_t limit_ns, void* stream);
+
 /* ---- sharing / reveal (§5.1, App. D.1.1) --------------------------------- */
 
 /* Encode and share reals.  x: device double[n].  shares: device u64 [P][n].
@@ -217,7 +232,10 @@ int mpc_beaver_mul(int P, int64_t n, const uint64_t* X, const uint64_t* Y, const
 /* Beaver matmul: X [P][M][K], Y [P][K][N], triple A [P][M][K], B [P][K][N],
  * C [P][M][N], Z [P][M][N] (device).  Z_p = C_p + E B_p + A_p F (+ E F on
  * party 0) with E = sum(X - A), F = sum(Y - B), optionally truncated by
- * trunc_bits.  ws: device workspace of mpc_matmul_workspace_size() bytes. */
+ * trunc_bits.  ws: device workspace of mpc_matmul_workspace_size() bytes.
+ * K = 0 gives Z = C (truncated); X, Y, A, B are then empty and may be NULL.
+ * Each of M*K, K*N and M*N must be at most 2^52 words (MPC_EUNSUPPORTED
+ * otherwise; the workspace-size functions return 0 for such shapes). */
 size_t mpc_matmul_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo);
 int mpc_beaver_matmul(int P, int64_t M, int64_t N, int64_t K, const uint64_t* X,
                       const uint64_t* Y, const uint64_t* A, const uint64_t* B,
@@ -242,7 +260,10 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
  * M*K + 2*K*N words (each region rounded up to 32 words), lives in a fixed
  * library-owned device array of MPC_NOALLOC_SCRATCH_WORDS words (8 MiB),
  * present on every device that loads the library until the process exits;
- * larger requests return MPC_ENOMEM and launch nothing.  It calls no
+ * larger requests return MPC_ENOMEM and launch nothing (the dimensions are
+ * bounded against the array before any product of them is formed, so no
+ * shape can wrap the size check).  Its protocol counters are those of
+ * mpc_beaver_matmul.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.  The first call on a
  * device looks up the array's device address (with that device current), so
  * make that first call before any stream capture.  All calls share the array
@@ -389,31 +410,37 @@ int mpc_global_avgpool(int P, int64_t rows, int64_t hw, const uint64_t* X, uint6
 
 /* ---- binary shares and comparison (§5.1-5.2, App. D.1.2-D.1.4) ---------- */
 
-/* A2B for P = 2: arith [2][n] -> binary [2][n] (device).  Each party's share
- * y_q is binary-shared with the ZERO_BIN stream (sub = q): party p holds
- * M_{q,p} ^ M_{q,(p-1) mod 2} ^ (p == q ? y_q : 0); the two binary-shared
- * words are added by a 64-bit Kogge-Stone adder whose 12 secret ANDs use
- * and_triples [12][3][2][n] (mpc_ttp_and_triples) in the order: generate,
- * then for d = 1, 2, 4, 8, 16, 32 the G-update and (d < 32) the P-update. */
+/* A2B (§5.1, App. D.1.3) for P = 2..8: arith [P][n] -> binary [P][n]
+ * (device).  Each party's share y_q is binary-shared with the ZERO_BIN stream
+ * (sub = q): party p holds M_{q,p} ^ M_{q,(p-1) mod P} ^ (p == q ? y_q : 0).
+ * P = 2: the two binary-shared words are added by one 64-bit Kogge-Stone
+ * adder whose 12 secret ANDs use and_triples [12][3][2][n]
+ * (mpc_ttp_and_triples) in the order: generate, then for d = 1, 2, 4, 8, 16,
+ * 32 the G-update and (d < 32) the P-update.  P = 3..8: a tree of adders;
+ * each level adds neighbours (0, 1), (2, 3), ... and passes an odd last
+ * addend up; adder a (numbered level by level, left to right) uses gates
+ * 12a .. 12a + 11 of and_triples [12 (P-1)][3][P][n].  7 rounds per level.
+ * P = 1 returns MPC_EUNSUPPORTED. */
 int mpc_a2b(int P, int64_t n, const uint64_t* arith, uint64_t* binary,
             const uint64_t* and_triples, uint64_t seed, uint64_t op_id, void* stream);
 
-/* Private ReLU for P = 2, fused in one kernel: [x > 0] = B2A(MSB(A2B(-x)))
+/* Private ReLU for P = 2..8 in one kernel: [x > 0] = B2A(MSB(A2B(-x)))
  * (comparator of §5.2, Alg. 2), then Y = Beaver product of X with the 0/1
- * mask (not truncated).  X, Y device u64 [2][n] (may alias); and_triples
- * [12][3][2][n]; r_arith [2][n] and r_bin [2][(n+63)/64] from
- * mpc_ttp_b2a_bits; mul_triple [3][2][n] = (A, B, C) from mpc_ttp_mul_triple
- * laid out consecutively.  (seed, op_id) drive the A2B binary zero-shares. */
+ * mask (not truncated).  X, Y device u64 [P][n] (may alias); and_triples
+ * [12 (P-1)][3][P][n] (the adder or adder tree of mpc_a2b); r_arith [P][n]
+ * and r_bin [P][(n+63)/64] from mpc_ttp_b2a_bits; mul_A, mul_B, mul_C
+ * [P][n] each, the elementwise triple from mpc_ttp_mul_triple.  (seed,
+ * op_id) drive the A2B binary zero-shares.  P = 1 returns MPC_EUNSUPPORTED. */
 int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
                      const uint64_t* and_triples, const uint64_t* r_arith,
-                     const uint64_t* r_bin, const uint64_t* mul_triple, uint64_t seed,
-                     uint64_t op_id, void* stream);
+                     const uint64_t* r_bin, const uint64_t* mul_A, const uint64_t* mul_B,
+                     const uint64_t* mul_C, uint64_t seed, uint64_t op_id, void* stream);
 
 /* Private ReLU with the dealer fused in (P = 2): the same result as
  *   mpc_ttp_and_triples(2, n, 12, seed, op_id) -> T,
  *   mpc_ttp_b2a_bits(2, n, seed, op_id + 1) -> r_arith, r_bin,
  *   mpc_ttp_mul_triple(2, n, seed, op_id + 2) -> A, B, C,
- *   mpc_private_relu(2, n, X, Y, T, r_arith, r_bin, [A B C], seed, op_id + 3),
+ *   mpc_private_relu(2, n, X, Y, T, r_arith, r_bin, A, B, C, seed, op_id + 3),
  * bit for bit, but every piece of dealer material is regenerated in registers
  * from its Philox stream instead of being written to and read from memory
  * (the trusted dealer and both parties are simulated in one kernel).  X, Y

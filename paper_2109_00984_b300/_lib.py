@@ -44,6 +44,7 @@ SIGNATURES = {
     "mpc_profile_reset": (c_int, []),
     "mpc_profile_read": (c_int, [ctypes.c_char_p, _P(ctypes.c_uint64), _P(ctypes.c_double)]),
     "mpc_profile_busy": (c_int, [ctypes.c_char_p, _P(ctypes.c_double)]),
+    "mpc_test_wait_timeout": (c_int, [c_i64, c_vp]),
     "mpc_ring_share": (c_int, [c_vp, c_i64, c_int, c_int, c_int, c_u64, c_u64, c_vp, c_vp]),
     "mpc_ring_share_encoded": (c_int, [c_vp, c_i64, c_int, c_int, c_u64, c_u64, c_vp, c_vp]),
     "mpc_reveal": (c_int, [c_vp, c_int, c_i64, c_int, c_vp, c_vp, c_vp]),
@@ -102,8 +103,8 @@ SIGNATURES = {
     "mpc_global_avgpool": (c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "mpc_truncate": (c_int, [c_int, c_i64, c_vp, c_int, c_i64, c_vp]),
     "mpc_a2b": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_u64, c_u64, c_vp]),
-    "mpc_private_relu": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64,
-                                 c_vp]),
+    "mpc_private_relu": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                 c_u64, c_u64, c_vp]),
 }
 
 _lib = None

@@ -409,16 +409,15 @@ def a2b(X, and_triples, seed, op_id, out=None):
 
 
 def private_relu(X, and_triples, r_arith, r_bin, mul_triple, seed, op_id, out=None):
-    """mul_triple: a [3, P, n] tensor (A, B, C stacked) or a tuple of three [P, n]."""
+    """mul_triple: the elementwise triple (A, B, C), each [P, n]-shaped (or a [3, P, n]
+    tensor, whose three slices are passed as they lie)."""
     P = X.shape[0]
     n = X.numel() // P
-    if isinstance(mul_triple, (tuple, list)):
-        mt = torch.stack([t.reshape(P, n) for t in mul_triple])
-    else:
-        mt = mul_triple
+    MA, MB, MC = mul_triple[0], mul_triple[1], mul_triple[2]
     out = torch.empty_like(X) if out is None else out
     _check(_L().mpc_private_relu(P, n, _ptr(X), _ptr(out), _ptr(and_triples), _ptr(r_arith),
-                                 _ptr(r_bin), _ptr(mt), seed, op_id, _stream()))
+                                 _ptr(r_bin), _ptr(MA, "mul A"), _ptr(MB, "mul B"),
+                                 _ptr(MC, "mul C"), seed, op_id, _stream()))
     return out
 
 

@@ -81,11 +81,19 @@ int validate(int P, int count, const mpc_matmul_desc* descs, int algo) {
   MPC_REQUIRE(count == 0 || descs != nullptr, "null descriptor array");
   MPC_REQUIRE(algo == MPC_ALGO_PLAIN || algo == MPC_ALGO_LIMB || algo == MPC_ALGO_AUTO,
               "unknown algo %d", algo);
+  // Opened words of the whole batch, bounded as they accumulate so that the
+  // workspace sum over all products cannot wrap.
+  i64 opened = 0;
   for (int i = 0; i < count; ++i) {
     const mpc_matmul_desc& d = descs[i];
     MPC_REQUIRE(d.M >= 1 && d.N >= 1 && d.K >= 1, "product %d: dimensions must be >= 1", i);
     MPC_REQUIRE(d.M <= (1ll << 31) && d.N <= (1ll << 31) && d.K <= (1ll << 31),
                 "product %d: dimension too large", i);
+    if (!gemm_shape_fits(d.M, d.N, d.K))
+      return fail(MPC_EUNSUPPORTED, "product %d: M*K, K*N or M*N exceeds 2^52 words", i);
+    opened += d.M * d.K + 2 * d.K * d.N;
+    if (opened > kMaxWords)
+      return fail(MPC_EUNSUPPORTED, "batch too large: opened operands exceed 2^52 words");
     MPC_REQUIRE(d.X && d.Y && d.A && d.B && d.C && d.Z, "product %d: null pointer", i);
   }
   return MPC_OK;

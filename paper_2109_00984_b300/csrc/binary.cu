@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
                                                         const u64* __restrict__ T,
                                                         const u64* __restrict__ r_arith,
                                                         const u64* __restrict__ r_bin,
-                                                        const u64* __restrict__ MT, u64 seed,
+                                                        const u64* __restrict__ MA,
+                                                        const u64* __restrict__ MB,
+                                                        const u64* __restrict__ MC, u64 seed,
                                                         u64 op_id) {
   const i64 nblk = ceil_div(n, 4);
   const i64 nw = ceil_div(n, 64);
@@ -210,12 +212,12 @@ __global__ void __launch_bounds__(kThreads) relu_kernel(i64 n, const u64* X, u64
         C1.v[j] = (a0.v[j] + a1.v[j]) * (b0.v[j] + b1.v[j]) - c0.v[j];
       }
     } else {
-      A0 = load4(MT, i0, n);
-      A1 = load4(MT + n, i0, n);
-      B0 = load4(MT + 2 * n, i0, n);
-      B1 = load4(MT + 3 * n, i0, n);
-      C0 = load4(MT + 4 * n, i0, n);
-      C1 = load4(MT + 5 * n, i0, n);
+      A0 = load4(MA, i0, n);
+      A1 = load4(MA + n, i0, n);
+      B0 = load4(MB, i0, n);
+      B1 = load4(MB + n, i0, n);
+      C0 = load4(MC, i0, n);
+      C1 = load4(MC + n, i0, n);
     }
     Quad y0, y1;
 #pragma unroll
@@ -387,7 +389,9 @@ __global__ void __launch_bounds__(128) relu_tree_kernel(i64 n, const u64* X, u64
                                                         const u64* __restrict__ T,
                                                         const u64* __restrict__ r_arith,
                                                         const u64* __restrict__ r_bin,
-                                                        const u64* __restrict__ MT, u64 seed,
+                                                        const u64* __restrict__ MA,
+                                                        const u64* __restrict__ MB,
+                                                        const u64* __restrict__ MC, u64 seed,
                                                         u64 op_id) {
   const i64 nw = ceil_div(n, 64);
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
@@ -409,14 +413,14 @@ __global__ void __launch_bounds__(128) relu_tree_kernel(i64 n, const u64* X, u64
     for (int p = 0; p < P; ++p) {
       const u64 ra = r_arith[(i64)p * n + i];
       bit[p] = ra - 2ull * z * ra + (p == 0 ? z : 0ull);
-      A[p] = MT[(i64)p * n + i];
-      B[p] = MT[(i64)(P + p) * n + i];
+      A[p] = MA[(i64)p * n + i];
+      B[p] = MB[(i64)p * n + i];
       E += x.v[p] - A[p];
       F += bit[p] - B[p];
     }
 #pragma unroll
     for (int p = 0; p < P; ++p)
-      Y[(i64)p * n + i] = MT[(i64)(2 * P + p) * n + i] + E * B[p] + A[p] * F +
+      Y[(i64)p * n + i] = MC[(i64)p * n + i] + E * B[p] + A[p] * F +
                           (p == 0 ? E * F : 0ull);
   }
 }
@@ -459,8 +463,9 @@ void launch_a2b_tree(i64 n, const u64* X, u64* B, const u64* T, u64 seed, u64 op
 
 template <int P>
 void launch_relu_tree(i64 n, const u64* X, u64* Y, const u64* T, const u64* ra, const u64* rb,
-                      const u64* MT, u64 seed, u64 op, cudaStream_t s) {
-  relu_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, Y, T, ra, rb, MT, seed, op);
+                      const u64* MA, const u64* MB, const u64* MC, u64 seed, u64 op,
+                      cudaStream_t s) {
+  relu_tree_kernel<P><<<grid_for(n, 128), 128, 0, s>>>(n, X, Y, T, ra, rb, MA, MB, MC, seed, op);
 }
 
 // Rounds of the adder tree: 7 per level, ceil(log2 P) levels.
@@ -523,19 +528,20 @@ int mpc_a2b(int P, int64_t n, const uint64_t* arith, uint64_t* binary,
 
 int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
                      const uint64_t* and_triples, const uint64_t* r_arith,
-                     const uint64_t* r_bin, const uint64_t* mul_triple, uint64_t seed,
-                     uint64_t op_id, void* stream) {
+                     const uint64_t* r_bin, const uint64_t* mul_A, const uint64_t* mul_B,
+                     const uint64_t* mul_C, uint64_t seed, uint64_t op_id, void* stream) {
   if (P == 1) return fail(MPC_EUNSUPPORTED, "private ReLU needs at least two parties");
   MPC_CHECK_PARTIES(P);
   MPC_REQUIRE(n >= 0, "negative length");
   if (n == 0) return MPC_OK;
-  MPC_REQUIRE(X && Y && and_triples && r_arith && r_bin && mul_triple, "null pointer");
+  MPC_REQUIRE(X && Y && and_triples && r_arith && r_bin && mul_A && mul_B && mul_C,
+              "null pointer");
   if (P > 2) {
     {
       KernelTimer timer("private_relu", as_stream(stream));
       MPC_DISPATCH_P3(P, launch_relu_tree, n, (const u64*)X, (u64*)Y, (const u64*)and_triples,
-                      (const u64*)r_arith, (const u64*)r_bin, (const u64*)mul_triple, seed, op_id,
-                      as_stream(stream));
+                      (const u64*)r_arith, (const u64*)r_bin, (const u64*)mul_A,
+                      (const u64*)mul_B, (const u64*)mul_C, seed, op_id, as_stream(stream));
     }
     int rc = check_launch("private_relu (adder tree)");
     if (rc == MPC_OK)
@@ -549,7 +555,7 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
     KernelTimer timer("private_relu", as_stream(stream));
     relu_kernel<false><<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, as_stream(stream)>>>(
         n, (const u64*)X, (u64*)Y, (const u64*)and_triples, (const u64*)r_arith,
-        (const u64*)r_bin, (const u64*)mul_triple, seed, op_id);
+        (const u64*)r_bin, (const u64*)mul_A, (const u64*)mul_B, (const u64*)mul_C, seed, op_id);
     rc = check_launch("private_relu");
   }
   if (rc == MPC_OK)

@@ -151,14 +151,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait for the phase of `bar` with the given parity.  Returns false
 // (and raises the CTA's abort flag) when the limit passes or another role
 // already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer() - t0 > kWaitLimitNs) {
+      if (globaltimer() - t0 > limit_ns) {
         *abort_flag = 1;
         return false;
       }
@@ -780,6 +781,26 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
     planes_b_tile(tile, pl.jb.j[z], pl.N, pl.K, pl.Kp, bx, by);
 }
 
+// Diagnostic for the bounded-wait status path: one thread waits, through
+// mbar_wait and the CTA abort flag exactly as the engine's roles do, for the
+// first phase of an mbarrier that nothing ever arrives at; the wait gives up
+// after limit_ns and the CTA records MPC_ETIMEOUT the way limb_gemm_kernel does
+// on an abort.  No copy, MMA or TMEM allocation is ever outstanding here, so
+// the timeout path can be run on a GPU without any risk to the context.
+__global__ void __launch_bounds__(32) wait_timeout_kernel(int* status,
+                                                          unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, &abort_flag, limit_ns))
+    record_status(status, MPC_ETIMEOUT);
+}
+
 // ---- host side -----------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -964,3 +985,13 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
 }
 
 }  // namespace mpc
+
+extern "C" int mpc_test_wait_timeout(int64_t limit_ns, void* stream) {
+  using namespace mpc;
+  MPC_REQUIRE(limit_ns >= 1000 && limit_ns <= 1000000000ll,
+              "limit_ns %lld outside [1 us, 1 s]", (long long)limit_ns);
+  int* st = device_status_ptr();
+  if (!st) return fail(MPC_ECUDA, "device status word unavailable");
+  wait_timeout_kernel<<<1, 32, 0, as_stream(stream)>>>(st, (unsigned long long)limit_ns);
+  return check_launch("wait_timeout");
+}

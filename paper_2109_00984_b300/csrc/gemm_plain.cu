@@ -26,7 +26,9 @@ __device__ __forceinline__ void plain_tile(const GemmJob& job, i64 M, i64 N, i64
                                            int trunc_bits, u64* part,
                                            u64 (*As)[BK][BM + APAD], u64 (*Bs)[BK][BN]) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const i64 ktiles = ceil_div(K, BK);
+  // K tiles of one pair; at least 1 so that the pair split below never
+  // divides by zero when K = 0 (then no tile is in range and Z = C).
+  const i64 ktiles = K > 0 ? ceil_div(K, BK) : 1;
 
   // Global-load coordinates.
   const int a_r = tid >> 1, a_k = (tid & 1) * 4;   // A: row a_r, 4 consecutive k

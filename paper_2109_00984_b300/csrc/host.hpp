@@ -23,6 +23,20 @@ int* device_status_ptr();
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Size guard, applied before any size arithmetic on a caller's shape.  Every
+// workspace formula of the library is a handful of terms M*K, K*N, M*N (or a
+// convolution's data size) times 8 bytes and at most 2 * MPC_MAX_PARTIES, so
+// with each such product at most kMaxWords = 2^52 words no formula can wrap
+// 64 bits.  mul_fits(a, b): a, b >= 0 and a * b <= kMaxWords, tested without
+// forming the product.
+constexpr long long kMaxWords = 1ll << 52;
+inline bool mul_fits(long long a, long long b) {
+  return a >= 0 && b >= 0 && (a == 0 || b <= kMaxWords / a);
+}
+inline bool gemm_shape_fits(long long M, long long N, long long K) {
+  return mul_fits(M, K) && mul_fits(K, N) && mul_fits(M, N);
+}
+
 // Optional per-kernel timing (mpc_profile_enable): brackets one launch with a
 // pair of CUDA events on its stream when profiling is on, a no-op otherwise.
 class KernelTimer {

@@ -148,10 +148,23 @@ int validate_conv(const mpc_conv_desc* d, i64* ho, i64* wo) {
               "conv sizes must be positive");
   MPC_REQUIRE(d->stride_h >= 1 && d->stride_w >= 1, "conv strides must be >= 1");
   MPC_REQUIRE(d->pad_h >= 0 && d->pad_w >= 0, "conv padding must be >= 0");
+  const i64 lim = 1ll << 31;  // each field in int32 range, so the sums below cannot wrap
+  if (d->batch >= lim || d->c_in >= lim || d->h >= lim || d->w >= lim || d->c_out >= lim ||
+      d->kh >= lim || d->kw >= lim || d->stride_h >= lim || d->stride_w >= lim ||
+      d->pad_h >= lim || d->pad_w >= lim)
+    return fail(MPC_EUNSUPPORTED, "conv descriptor field at or above 2^31");
   MPC_REQUIRE(d->h + 2 * d->pad_h >= d->kh && d->w + 2 * d->pad_w >= d->kw,
               "kernel larger than the padded input");
   *ho = (d->h + 2 * d->pad_h - d->kh) / d->stride_h + 1;
   *wo = (d->w + 2 * d->pad_w - d->kw) / d->stride_w + 1;
+  // GEMM view M = c_out, K = c_in kh kw, N = batch ho wo and the data size, all
+  // bounded before any workspace formula multiplies them.
+  if (!mul_fits(d->c_in, d->kh) || !mul_fits(d->c_in * d->kh, d->kw) ||
+      !mul_fits(d->batch, *ho) || !mul_fits(d->batch * *ho, *wo) ||
+      !mul_fits(d->batch, d->c_in) || !mul_fits(d->batch * d->c_in, d->h) ||
+      !mul_fits(d->batch * d->c_in * d->h, d->w) ||
+      !gemm_shape_fits(d->c_out, d->batch * *ho * *wo, d->c_in * d->kh * d->kw))
+    return fail(MPC_EUNSUPPORTED, "conv shape too large (a size product exceeds 2^52 words)");
   return MPC_OK;
 }
 
@@ -248,7 +261,7 @@ using namespace mpc;
 extern "C" {
 
 size_t mpc_matmul_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo) {
-  if (P < 1 || P > MPC_MAX_PARTIES || M < 0 || N < 0 || K < 0) return 0;
+  if (P < 1 || P > MPC_MAX_PARTIES || !gemm_shape_fits(M, N, K)) return 0;
   return matmul_ws(P, M, N, K, resolve_algo(algo, M, N, K));
 }
 
@@ -259,9 +272,12 @@ int mpc_beaver_matmul(int P, int64_t M, int64_t N, int64_t K, const uint64_t* X,
   MPC_CHECK_PARTIES(P);
   if (int rc = check_algo(algo)) return rc;
   MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
+  if (!gemm_shape_fits(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "shape too large: M*K, K*N or M*N exceeds 2^52 words");
   MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
   if (M == 0 || N == 0) return MPC_OK;
-  MPC_REQUIRE(X && Y && A && B && C && Z, "null pointer");
+  // With K = 0 the operands and a, b are empty (never read) and may be NULL.
+  MPC_REQUIRE(C && Z && (K == 0 || (X && Y && A && B)), "null pointer");
   algo = resolve_algo(algo, M, N, K);
   if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
     return fail(MPC_EUNSUPPORTED, "limb engine does not support M=%lld N=%lld K=%lld",
@@ -385,7 +401,7 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
 }
 
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo) {
-  if (M < 0 || N < 0 || K < 0) return 0;
+  if (!gemm_shape_fits(M, N, K)) return 0;
   return engine_ws(resolve_algo(algo, M, N, K), M, N, K, 1, 1);
 }
 
@@ -394,6 +410,8 @@ int mpc_ring_gemm(int64_t M, int64_t N, int64_t K, const uint64_t* A, const uint
                   void* stream) {
   if (int rc = check_algo(algo)) return rc;
   MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
+  if (!gemm_shape_fits(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "shape too large: M*K, K*N or M*N exceeds 2^52 words");
   if (M == 0 || N == 0) return MPC_OK;
   MPC_REQUIRE(A && B && Z, "null pointer");
   algo = resolve_algo(algo, M, N, K);
@@ -414,7 +432,7 @@ int mpc_ring_gemm(int64_t M, int64_t N, int64_t K, const uint64_t* A, const uint
 }
 
 size_t mpc_matmul_triple_workspace_size(int P, int64_t M, int64_t N, int64_t K, int algo) {
-  if (P < 1 || P > MPC_MAX_PARTIES || M < 0 || N < 0 || K < 0) return 0;
+  if (P < 1 || P > MPC_MAX_PARTIES || !gemm_shape_fits(M, N, K)) return 0;
   return matmul_triple_ws(M, N, K, resolve_algo(algo, M, N, K));
 }
 
@@ -424,7 +442,9 @@ int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed,
   MPC_CHECK_PARTIES(P);
   if (int rc = check_algo(algo)) return rc;
   MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
-  MPC_REQUIRE(A && B && C, "null pointer");
+  if (!gemm_shape_fits(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "shape too large: M*K, K*N or M*N exceeds 2^52 words");
+  MPC_REQUIRE(C && ((A && B) || M * K + K * N == 0), "null pointer");
   algo = resolve_algo(algo, M, N, K);
   if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
     return fail(MPC_EUNSUPPORTED, "limb engine does not support this shape");

@@ -82,14 +82,27 @@ extern "C" int mpc_beaver_matmul_noalloc(int P, int64_t M, int64_t N, int64_t K,
   MPC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative dimension");
   MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
   if (M == 0 || N == 0) return MPC_OK;
-  MPC_REQUIRE(X && Y && A && B && C && Z, "null pointer");
-  // Scratch: E [M][K], F [K][N], G = B_0 + F [K][N].
-  const i64 need = round_words(M * K) + 2 * round_words(K * N);
-  if (M > (1ll << 40) || N > (1ll << 40) || K > (1ll << 40) || need > MPC_NOALLOC_SCRATCH_WORDS)
+  // With K = 0 the operands and a, b are empty (never read) and may be NULL.
+  MPC_REQUIRE(C && Z && (K == 0 || (X && Y && A && B)), "null pointer");
+  // Scratch: E [M][K], F [K][N], G = B_0 + F [K][N].  The dimensions are
+  // bounded against the scratch size first, so that M*K and K*N below cannot
+  // wrap: with K > 0, M*K <= W needs M <= W / K and 2*K*N <= W needs
+  // N <= W / (2K).  K = 0 needs no scratch (Z = C, truncated).
+  constexpr i64 W = MPC_NOALLOC_SCRATCH_WORDS;
+  if (K > W || (K > 0 && (M > W / K || N > W / (2 * K))))
     return fail(MPC_ENOMEM,
-                "mpc_beaver_matmul_noalloc: needs M*K + 2*K*N = %lld scratch words, the fixed "
-                "scratch holds %lld",
-                (long long)need, (long long)MPC_NOALLOC_SCRATCH_WORDS);
+                "mpc_beaver_matmul_noalloc: M=%lld N=%lld K=%lld needs more than the fixed "
+                "scratch of %lld words",
+                (long long)M, (long long)N, (long long)K, (long long)W);
+  const i64 need = round_words(M * K) + 2 * round_words(K * N);
+  if (need > W)
+    return fail(MPC_ENOMEM,
+                "mpc_beaver_matmul_noalloc: needs M*K + 2*K*N = %lld scratch words (each "
+                "region rounded up to 32), the fixed scratch holds %lld",
+                (long long)need, (long long)W);
+  // M*N stays unbounded by the scratch; it indexes the caller's C and Z.
+  if (!mul_fits(M, N))
+    return fail(MPC_EUNSUPPORTED, "mpc_beaver_matmul_noalloc: M*N exceeds 2^52 words");
   u64* scratch = nullptr;
   if (int rc = noalloc_scratch(&scratch)) return rc;
   u64* E = scratch;
@@ -119,5 +132,11 @@ extern "C" int mpc_beaver_matmul_noalloc(int P, int64_t M, int64_t N, int64_t K,
     g.jobs[p].C = (const u64*)C + (i64)p * M * N;
     g.jobs[p].Z = (u64*)Z + (i64)p * M * N;
   }
-  return launch_gemm_plain(g, s);
+  const int rc = launch_gemm_plain(g, s);
+  // The same protocol accounting as mpc_beaver_matmul: one round, E and F
+  // opened, the triple's words consumed, P GEMMs of two operand pairs.
+  if (rc == MPC_OK)
+    stats_add(1, 8ull * (uint64_t)(M * K + K * N), 0, (uint64_t)P * (M * K + K * N + M * N),
+              (uint64_t)P * 2ull * M * N * K);
+  return rc;
 }

@@ -54,14 +54,14 @@ def test_bad_party_counts_rejected(lib):
     assert lib.mpc_beaver_mul(9, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
     assert b"party count" in lib.mpc_last_error()
     assert lib.mpc_ring_share(FAKE, 10, 2, 2, 16, 1, 1, FAKE, NULL) == E["EINVAL"]   # src >= P
-    assert lib.mpc_private_relu(1, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_private_relu(1, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
     assert lib.mpc_a2b(1, 10, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EUNSUPPORTED"]
 
 
 def test_null_pointers_rejected(lib):
     assert lib.mpc_beaver_mul(2, 10, FAKE, NULL, FAKE, FAKE, FAKE, FAKE, NULL, NULL, 0, NULL) == E["EINVAL"]
     assert lib.mpc_reveal(FAKE, 2, 10, 16, NULL, NULL, NULL) == E["EINVAL"]
-    assert lib.mpc_private_relu(2, 10, FAKE, FAKE, NULL, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EINVAL"]
+    assert lib.mpc_private_relu(2, 10, FAKE, FAKE, NULL, FAKE, FAKE, FAKE, FAKE, FAKE, 1, 1, NULL) == E["EINVAL"]
 
 
 def test_bad_sizes_rejected(lib):
@@ -78,7 +78,7 @@ def test_bad_sizes_rejected(lib):
 def test_zero_length_is_a_no_op(lib):
     assert lib.mpc_beaver_mul(2, 0, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, 0, NULL) == E["OK"]
     assert lib.mpc_truncate(2, 0, NULL, 16, 0, NULL) == E["OK"]
-    assert lib.mpc_private_relu(2, 0, NULL, NULL, NULL, NULL, NULL, NULL, 1, 1, NULL) == E["OK"]
+    assert lib.mpc_private_relu(2, 0, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, 1, 1, NULL) == E["OK"]
 
 
 def test_workspace_too_small_rejected(lib):
@@ -108,3 +108,43 @@ def test_stats_counters_reset(lib):
     s = _lib.Stats()
     assert lib.mpc_get_stats(ctypes.byref(s)) == 0
     assert s.calls == 0 and s.rounds == 0
+
+
+def test_shape_products_bounded_before_size_arithmetic(lib):
+    from paper_2109_00984_b300 import _lib
+    big = 1 << 32   # M*K = K*N = M*N = 2^64 would wrap to 0 if multiplied unchecked
+    assert lib.mpc_matmul_workspace_size(2, big, big, big, 0) == 0
+    assert lib.mpc_matmul_triple_workspace_size(2, big, big, big, 0) == 0
+    assert lib.mpc_ring_gemm_workspace_size(big, big, big, 0) == 0
+    assert lib.mpc_beaver_matmul(2, big, big, big, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 0, 0, FAKE,
+                                 1 << 40, NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_ring_gemm(big, big, big, FAKE, FAKE, FAKE, FAKE, 0, FAKE, 1 << 40,
+                             NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_ttp_matmul_triple(2, big, big, big, 1, 1, FAKE, FAKE, FAKE, 0, FAKE, 1 << 40,
+                                     NULL) == E["EUNSUPPORTED"]
+    d = _lib.ConvDesc(1 << 20, 1 << 20, 1 << 12, 1 << 12, 4, 1, 1, 1, 1, 0, 0)  # 2^64 data words
+    assert lib.mpc_conv2d_workspace_size(2, ctypes.byref(d), 0) == 0
+    d = _lib.ConvDesc(1, 3, 5, 5, 1 << 31, 1, 1, 1, 1, 0, 0)                     # field >= 2^31
+    assert lib.mpc_conv2d_workspace_size(2, ctypes.byref(d), 0) == 0
+
+
+def test_noalloc_size_refused_before_any_device_work(lib):
+    # The scratch holds 2^20 words.  The refusal must come from the size check,
+    # before the device address lookup (which would fail differently here).
+    big = 1 << 32
+    assert lib.mpc_beaver_matmul_noalloc(2, big, big, big, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 16,
+                                         NULL) == E["ENOMEM"]
+    assert b"scratch" in lib.mpc_last_error()
+    # M*K = 2^19 + 32, 2*K*N = 2^19: 32 words over the scratch.
+    assert lib.mpc_beaver_matmul_noalloc(2, 16385, 8192, 32, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                         16, NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_matmul_noalloc(2, 1, 1, (1 << 20) + 1, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                         16, NULL) == E["ENOMEM"]
+    # Exactly 2^20 words is accepted by the size check (it then needs a device).
+    assert lib.mpc_beaver_matmul_noalloc(2, 16384, 8192, 32, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                         16, NULL) != E["ENOMEM"]
+
+
+def test_wait_timeout_limit_validated(lib):
+    assert lib.mpc_test_wait_timeout(10, NULL) == E["EINVAL"]
+    assert lib.mpc_test_wait_timeout(2_000_000_000, NULL) == E["EINVAL"]
