@@ -49,10 +49,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["plain", "limb", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements of the default line (GEMM sweep, "
+                         "HBM-bound kernels, ResNet-18, batched products)")
     ap.add_argument("--workload", default="speech",
-                    choices=["speech", "gemm", "batched", "resnet", "approx"],
+                    choices=["speech", "gemm", "batched", "resnet", "approx", "elementwise"],
                     help="speech: the private conv stack (default); gemm: ring GEMM sweep; "
-                         "batched: 512 uneven Beaver matmuls")
+                         "batched: 512 uneven Beaver matmuls; elementwise: the HBM-bound "
+                         "kernels at n = 2^20 .. 2^26")
     ap.add_argument("--sizes", default="1024,2048,4096,8192")
     return ap.parse_args()
 
@@ -370,7 +374,10 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    bf16_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    # The limb GEMM launches run 40-90 us each inside a ~1.4 ms step and a timed
+    # region of tens of ms, far from the seconds-long loop behind the sustained
+    # figure: the burst peak is their denominator.
+    bf16_peak = peaks.get("bf16_tflops", 1800.0)
     peak_src = "of measured" if peaks else "of fallback"
 
     macs = layer_macs(net)
@@ -397,7 +404,7 @@ def run_ours(args):
                 "traffic": LIMB_GEMM_DRAM_BYTES_PER_LAUNCH,
                 "traffic_note": "bytes per launch, mean of the 14 limb GEMM launches of one "
                                 "step (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
-                "peak_source": peak_src + " (bf16 sustained)",
+                "peak_source": peak_src + " (bf16 burst)",
                 "launches_per_step": launches / args.steps,
                 "busy_ms_per_step": kms / args.steps,
                 "launch_ms_sum_per_step": kms_sum / args.steps}
@@ -409,6 +416,16 @@ def run_ours(args):
         roof = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_tops,
                 "unit": "TOPS", "frac": achieved / peak_tops, "traffic": None,
                 "peak_source": "derived: 148 SM x 64 IMAD/clk x 2.032 GHz / 4 IMAD per ring MAC"}
+
+    extras = {}
+    if not args.no_extras and world == 1:
+        # Further measurements on the same box, after the timed region: the
+        # limb-vs-plain ring GEMM, the HBM-bound kernels, the ResNet-18 and
+        # batched workloads (each bounded to a few seconds).
+        extras["gemm_sweep"] = extra_gemm_sweep(dev, peaks)
+        extras["hbm_kernels"] = extra_hbm_kernels(dev, peaks, [1 << 26])
+        extras["resnet18"] = extra_resnet(dev, peaks, steps=3, warmup=1)
+        extras["batched"] = extra_batched(dev, reps=3)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # host baseline: rank 0 at N = 1 only
@@ -437,9 +454,161 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- extras
+# ALU roof of the plain engine: 148 SMs x 64 32-bit IMAD/clk x 2.032 GHz, 4 IMAD
+# issue slots per 64-bit ring MAC (lo x lo wide = 2, two cross products = 2).
+PLAIN_PEAK_TOPS = 148 * 64 * 2.032e9 / 4 * 2 / 1e12
+# Algorithmic HBM bytes per element of the two-party kernels (triples materialised):
+#   beaver_mul + trunc: read X, Y, A, B, C (5 x 16 B), write Z (16 B) = 96
+#   truncate (in place): read + write 16 B = 32
+#   a2b: read 16 B, 12 AND gates x (a, b, c) x 2 words = 576 B, write 16 B = 608
+#   private_relu: relu_bytes_per_elem() = 672.25
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def median_event_ms(fn, reps, flush=None, warm=1):
+    """Median device time (ms) of fn over `reps` calls, CUDA events on the current
+    stream, with `warm` untimed calls first and the L2 flushed before each timed
+    call when a flush buffer is given."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+
+def measure_ring_gemm(n, algo, dev, reps, flush, bf16_burst):
+    """One ring GEMM Z = A B, M = N = K = n, words uniform over Z/2^64 (seeded)."""
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+    g = torch.Generator(device=dev)
+    g.manual_seed(n)
+    A = torch.randint(-2 ** 63, 2 ** 63 - 1, (n, n), dtype=torch.int64, device=dev, generator=g)
+    B = torch.randint(-2 ** 63, 2 ** 63 - 1, (n, n), dtype=torch.int64, device=dev, generator=g)
+    Z = torch.empty((n, n), dtype=torch.int64, device=dev)
+    ws = torch.empty(max(1, mpc.ring_gemm_workspace_size(n, n, n, algo)), dtype=torch.uint8,
+                     device=dev)
+
+    def call():
+        mpc.ring_gemm(A, B, None, algo=algo, out=Z, ws=ws)
+
+    ms = median_event_ms(call, reps, flush)
+    rec = {"ms": ms, "ring_tops": 2 * n ** 3 / (ms / 1e3) / 1e12, "reps": reps}
+    if algo == mpc.LIMB:
+        mpc.profile_reset()
+        mpc.profile_enable(True)
+        for _ in range(reps):
+            flush.zero_()
+            call()
+        torch.cuda.synchronize()
+        mpc.profile_enable(False)
+        kl, kms = mpc.profile_read("gemm_limb")
+        pl, pms = mpc.profile_read("limb_planes")
+        k_ms = kms / max(kl, 1)
+        rec["mma_kernel_ms"] = k_ms
+        rec["planes_ms"] = pms / max(pl, 1)
+        rec["tensor_tflops"] = 72 * n ** 3 / (k_ms / 1e3) / 1e12   # 36 digit-pair MMAs per MAC
+        rec["tensor_frac"] = rec["tensor_tflops"] / bf16_burst
+        rec["tensor_frac_peak"] = "bf16 burst (the kernel is timed alone)"
+    else:
+        rec["alu_frac"] = rec["ring_tops"] / PLAIN_PEAK_TOPS
+        rec["alu_peak_ring_tops"] = PLAIN_PEAK_TOPS
+    del A, B, Z, ws
+    torch.cuda.empty_cache()
+    return rec
+
+
+def extra_gemm_sweep(dev, peaks, sizes=(4096, 8192), reps=5):
+    """Limb (tcgen05) vs plain (CUDA-core) ring GEMM at the largest sweep sizes."""
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+    burst = peaks.get("bf16_tflops", 1800.0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    out = {"workload": "ring GEMM M=N=K, uniform Z/2^64 words, L2 flushed between launches; "
+                       "limb: whole call (digit planes + MMA kernel); tensor_frac: MMA kernel "
+                       "at 72 n^3 digit-pair flops against the measured bf16 burst peak; "
+                       "plain: against its derived ALU roof "
+                       f"({PLAIN_PEAK_TOPS:.2f} ring TOPS)"}
+    for n in sizes:
+        limb = measure_ring_gemm(n, mpc.LIMB, dev, reps, flush, burst)
+        plain = measure_ring_gemm(n, mpc.PLAIN, dev, max(2, reps // 2), flush, burst)
+        out[str(n)] = {"limb": limb, "plain": plain, "limb_over_plain": plain["ms"] / limb["ms"]}
+    del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_hbm_kernels(dev, peaks, n, reps=5):
+    """The HBM-bound two-party kernels on n elements (inputs far larger than L2 from
+    n = 2^24 on, so no flush), GB/s of algorithmic bytes against the copy peak."""
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+
+    def words(shape):
+        return torch.randint(-2 ** 63, 2 ** 63 - 1, shape, dtype=torch.int64, device=dev,
+                             generator=g)
+
+    def rec(name, ms, bpe):
+        gbs = bpe * n / (ms / 1e3) / 1e9
+        return {"ms": ms, "bytes_per_elem": bpe, "gbs": gbs, "frac": gbs / hbm}
+
+    res = {}
+    X, Y = words((2, n)), words((2, n))
+    A, B, C = mpc.ttp_mul_triple(2, n, 1, 11, device=dev)
+    Z = torch.empty_like(X)
+    res["beaver_mul_trunc"] = rec("beaver_mul_trunc", median_event_ms(
+        lambda: mpc.beaver_mul(X, Y, A, B, C, trunc_bits=16, out=Z), reps), 96.0)
+    res["truncate"] = rec("truncate", median_event_ms(lambda: mpc.truncate(Z, 16), reps), 32.0)
+    del Y, A, B, C
+    T = mpc.ttp_and_triples(2, n, 1, 12, device=dev)
+    res["a2b"] = rec("a2b", median_event_ms(lambda: mpc.a2b(X, T, 1, 13, out=Z), reps), 608.0)
+    ra, rb = mpc.ttp_b2a_bits(2, n, 1, 14, device=dev)
+    MT = torch.empty((3, 2, n), dtype=torch.int64, device=dev)
+    mpc.ttp_mul_triple(2, n, 1, 15, out=(MT[0], MT[1], MT[2]))
+    res["private_relu"] = rec("private_relu", median_event_ms(
+        lambda: mpc.private_relu(X, T, ra, rb, MT, 1, 16, out=Z), reps), relu_bytes_per_elem())
+    del X, Z, T, ra, rb, MT
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_hbm_kernels(dev, peaks, sizes, reps=5):
+    out = {"workload": "two-party HBM-bound kernels, triples materialised; GB/s of algorithmic "
+                       "bytes per element (beaver_mul+trunc 96, truncate 32, a2b 608, "
+                       f"private_relu {relu_bytes_per_elem():.2f}) against the measured copy "
+                       "bandwidth; inputs > L2"}
+    for n in sizes:
+        out[f"2^{int(np.log2(n))}"] = measure_hbm_kernels(dev, peaks, n, reps)
+    return out
 
 
 def run_gemm_sweep(args):
@@ -507,6 +676,18 @@ def run_gemm_sweep(args):
 
 
 def run_batched(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps(measure_batched(dev, max(3, min(args.steps, 10)))), flush=True)
+
+
+def extra_batched(dev, reps=3):
+    r = measure_batched(dev, reps)
+    return r
+
+
+def measure_batched(dev, reps):
     """512 two-party Beaver matmuls with (M, N, K) log-uniform in [32, 2048] (seed 2).
 
     Times the online step (opening + products + truncation; triples dealt
@@ -518,8 +699,6 @@ def run_batched(args):
 
     import paper_2109_00984_b300 as mpc
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     P = 2
     dims = synth.batched_dims()
     gen = torch.Generator(device=dev)
@@ -562,7 +741,6 @@ def run_batched(args):
             mpc.beaver_matmul(X, Y, A, B, C, algo=mpc.AUTO, trunc_bits=16, out=Z, ws=w)
 
     per_product()
-    reps = max(3, min(args.steps, 10))
     t_each = timed(per_product, reps)
 
     # (b) one batched call, autotuned routing
@@ -595,10 +773,25 @@ def run_batched(args):
             "speedup_graph_vs_per_product": t_each / t_graph,
             "tuned_limb_min_macs": tune.limb_min_macs,
             "kernel_launches_per_batched_call": launches}
-    print(json.dumps(line), flush=True)
+    del prods, bm, g
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_resnet(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps(measure_resnet(dev, load_peaks(), args.steps, args.warmup)), flush=True)
+
+
+def extra_resnet(dev, peaks, steps=3, warmup=1):
+    r = measure_resnet(dev, peaks, steps, warmup)
+    r.pop("clocks", None)
+    return r
+
+
+def measure_resnet(dev, peaks, steps_arg, warmup):
     """Private inference of the ResNet-18-shaped CNN: 2 parties, batch 8 of 3x224x224.
 
     One step = share the batch, deal and consume all material of every layer
@@ -610,18 +803,16 @@ def run_resnet(args):
     import paper_2109_00984_b300 as mpc
     from paper_2109_00984_b300.resnet import PrivateResNet18
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     batch = 8
     x = torch.from_numpy(synth.resnet_input(batch=batch, hw=224)).to(dev)
     sched = synth.resnet_schedule()
     net = PrivateResNet18(synth.resnet_weights(), synth.RESNET18, sched, algo=mpc.AUTO, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-    for w in range(max(1, args.warmup)):
+    for w in range(max(1, warmup)):
         net.reveal(net.forward(x, synth.resnet_schedule(step=100 + w)))
     torch.cuda.synchronize()
-    steps = max(1, args.steps)
+    steps = max(1, steps_arg)
 
     def timed_pass(first_step, profiled):
         mpc.profile_reset()
@@ -649,7 +840,7 @@ def run_resnet(args):
     stats = mpc.get_stats()
     graphs[0][0].replay()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.5)
     ms = timed_pass(0, False)     # headline: uninstrumented graph replays
@@ -659,15 +850,31 @@ def run_resnet(args):
                                                  "private_relu", "private_relu_fused",
                                                  "gemm_plain_batched")}
     busy = {k: mpc.profile_busy(k) for k in prof}
+    # Every ResNet-18 product at batch 8 is above the AUTO threshold, so all ring
+    # MACs run on the limb engine: the online products count P x 2 pairs x MNK
+    # (the library counter), the dealer's c = a b one pair more per product.
+    online_macs = stats["ring_macs"] / steps
+    limb_macs = online_macs * (1 + 1 / 4)
+    kern = max(busy, key=lambda k: busy[k])
+    roof = {"kernel": kern, "busy_ms_per_step": busy[kern] / steps}
+    if kern == "gemm_limb":
+        tf = 72 * limb_macs / (busy[kern] / steps / 1e3) / 1e12
+        roof.update({"bound": "tensor", "achieved": tf, "unit": "TFLOP/s",
+                     "peak": peaks.get("bf16_tflops", 1800.0),
+                     "frac": tf / peaks.get("bf16_tflops", 1800.0),
+                     "peak_source": "of measured (bf16 burst)"})
     line = {"workload": "private ResNet-18-shaped inference, 2 parties, batch 8 x 3x224x224, "
-                        "He-init weights, dealer in the step",
+                        "He-init weights, dealer in the step, one CUDA-graph replay per step",
             "value": batch / (ms / 1e3), "unit": "images/s", "ms_per_step": ms, "steps": steps,
             "paper_context_images_per_s": 1 / 2.49,
             "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0]},
             "kernel_busy_ms_per_step": {k: busy[k] / steps for k, v in prof.items() if v[0]},
-            "ring_macs_per_step": stats["ring_macs"] / steps,
+            "ring_macs_per_step": online_macs + online_macs / 4,
+            "roofline": roof,
             "gpu_launches_per_step": stats["launches"] / steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    del net, graphs
+    torch.cuda.empty_cache()
+    return line
 
 
 # Philox4x64-10 blocks each fused function regenerates per element (one quad_gen
@@ -769,8 +976,25 @@ def run_approx(args):
     print(json.dumps(line), flush=True)
 
 
+def run_elementwise(args):
+    """The HBM-bound kernels swept over n = 2^20 .. 2^26 (two parties)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = load_peaks()
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = extra_hbm_kernels(dev, peaks, [1 << e for e in range(20, 27, 2)],
+                            reps=max(3, args.steps))
+    res["clocks"] = clocks.stop()
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "elementwise" and args.impl != "reference":
+        run_elementwise(args)
+        return
     if args.workload == "resnet" and args.impl != "reference":
         run_resnet(args)
         return

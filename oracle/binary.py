@@ -105,15 +105,17 @@ def binary_share_of_share(arith, q, seed, op_id):
 
 
 def a2b(arith, and_triples, seed, op_id, tr=None):
-    """[x] -> <x>; arith [P][n] (P >= 2), returns binary shares [P][n].
+    """[x] -> <x>; arith [P][n], returns binary shares [P][n].
 
     and_triples: [12 (P - 1)][3][P][n], twelve gates per adder of the tree.
+    The tree has ceil(log2 P) levels; for P = 1 it has none, and the single
+    party's binary sharing of its own share (the masks cancel) is the result.
     """
     arith = np.asarray(arith, dtype=U64)
     P = arith.shape[0]
-    if P < 2:
-        raise ValueError("A2B needs at least two parties")
-    T = np.asarray(and_triples, dtype=U64)
+    if P < 1:
+        raise ValueError("A2B needs at least one party")
+    T = np.asarray(and_triples, dtype=U64) if P > 1 else None
     vals = [binary_share_of_share(arith, q, seed, op_id) for q in range(P)]
     adder = 0
     while len(vals) > 1:

@@ -82,9 +82,15 @@ def test_a2b_reconstructs_the_secret(rng):
     assert tr.rounds == 7     # Table 3: log2|P| * log2(bits) = 1 * 6, +1 generate
 
 
-def test_a2b_rejects_one_party():
+def test_a2b_one_party_is_the_identity():
+    """A tree of ceil(log2 1) = 0 adder levels: the binary sharing of the one
+    share is the share itself, with no AND gate and no round."""
+    x = np.array([[0, 1, M64, 1 << 63, 12345]], dtype=np.uint64)
+    tr = Transcript()
+    assert np.array_equal(binary.a2b(x, np.zeros((0, 3, 1, 5), dtype=np.uint64), 1, 1, tr), x)
+    assert tr.rounds == 0
     with pytest.raises(ValueError):
-        binary.a2b(np.zeros((1, 4), dtype=np.uint64), None, 1, 1)
+        binary.a2b(np.zeros((0, 4), dtype=np.uint64), None, 1, 1)
 
 
 @pytest.mark.parametrize("P,levels", [(3, 2), (4, 2), (5, 3), (8, 3)])
