@@ -752,6 +752,22 @@ def measure_batched(dev, reps):
     t_batched = timed(bm, reps)
     launches = mpc.get_stats()["launches"] / reps
 
+    # per-kernel device time of one batched call (the library's launch events)
+    mpc.profile_reset()
+    mpc.profile_enable(True)
+    for _ in range(reps):
+        flush.zero_()
+        bm()
+    torch.cuda.synchronize()
+    mpc.profile_enable(False)
+    kernels = {}
+    for k in ("batched_open", "gemm_plain_batched", "limb_planes", "gemm_limb"):
+        n_l, ms_k = mpc.profile_read(k)
+        if n_l:
+            kernels[k] = ms_k / reps
+    limb_macs = float(sum(2 * P * int(M) * int(N) * int(K) for M, N, K in dims
+                          if float(M) * float(N) * float(K) >= tune.limb_min_macs))
+
     # (c) the batched call captured in a CUDA graph
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -772,6 +788,10 @@ def measure_batched(dev, reps):
             "graph_ring_tops": ring_ops / (t_graph / 1e3) / 1e12,
             "speedup_graph_vs_per_product": t_each / t_graph,
             "tuned_limb_min_macs": tune.limb_min_macs,
+            "kernel_ms_per_call": kernels,
+            "limb_tensor_frac": (72 * limb_macs / (kernels["gemm_limb"] / 1e3) / 1e12 /
+                                 load_peaks().get("bf16_tflops", 1800.0))
+            if kernels.get("gemm_limb") else None,
             "kernel_launches_per_batched_call": launches}
     del prods, bm, g
     torch.cuda.empty_cache()
@@ -857,12 +877,23 @@ def measure_resnet(dev, peaks, steps_arg, warmup):
     limb_macs = online_macs * (1 + 1 / 4)
     kern = max(busy, key=lambda k: busy[k])
     roof = {"kernel": kern, "busy_ms_per_step": busy[kern] / steps}
+    relu_elems = stats["and_gates"] / 12 / steps      # 12 secret ANDs per two-party ReLU
     if kern == "gemm_limb":
         tf = 72 * limb_macs / (busy[kern] / steps / 1e3) / 1e12
         roof.update({"bound": "tensor", "achieved": tf, "unit": "TFLOP/s",
                      "peak": peaks.get("bf16_tflops", 1800.0),
                      "frac": tf / peaks.get("bf16_tflops", 1800.0),
                      "peak_source": "of measured (bf16 burst)"})
+    elif kern == "private_relu_fused":
+        # ALU-bound: 17 Philox4x64-10 blocks regenerated per element
+        gb = RELU_FUSED_BLOCKS * relu_elems / (busy[kern] / steps / 1e3) / 1e9
+        roof.update({"bound": "alu", "achieved": gb, "unit": "G Philox blocks/s",
+                     "peak": PHILOX_PEAK_BLOCKS / 1e9, "frac": gb * 1e9 / PHILOX_PEAK_BLOCKS,
+                     "peak_source": "derived: 64 32-bit multiply results/clk/SM, 148 SMs, "
+                                    "2032 MHz, 160 per Philox4x64-10 block"})
+    if "gemm_limb" in busy and kern != "gemm_limb":
+        tf = 72 * limb_macs / (busy["gemm_limb"] / steps / 1e3) / 1e12
+        roof["gemm_limb_tensor_frac"] = tf / peaks.get("bf16_tflops", 1800.0)
     line = {"workload": "private ResNet-18-shaped inference, 2 parties, batch 8 x 3x224x224, "
                         "He-init weights, dealer in the step, one CUDA-graph replay per step",
             "value": batch / (ms / 1e3), "unit": "images/s", "ms_per_step": ms, "steps": steps,
@@ -870,6 +901,7 @@ def measure_resnet(dev, peaks, steps_arg, warmup):
             "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0]},
             "kernel_busy_ms_per_step": {k: busy[k] / steps for k, v in prof.items() if v[0]},
             "ring_macs_per_step": online_macs + online_macs / 4,
+            "relu_elements_per_step": relu_elems,
             "roofline": roof,
             "gpu_launches_per_step": stats["launches"] / steps, "clocks": clk}
     del net, graphs
@@ -877,6 +909,11 @@ def measure_resnet(dev, peaks, steps_arg, warmup):
     return line
 
 
+# Philox4x64-10 blocks the fused private ReLU regenerates per element (one
+# quad_gen = one block per element): the A2B masks 1, the AND gates' a/b words
+# 12, their c_0 words 3, the B2A pair (with the triple's c_0) 1, the triple's
+# a/b words 1.
+RELU_FUSED_BLOCKS = 18
 # Philox4x64-10 blocks each fused function regenerates per element (one quad_gen
 # call = one block per element): exp = 2 chunks of 3; a product = 5/4, a square
 # = 3/4; a comparison = 16; see the kernels' word lists.

@@ -131,8 +131,9 @@ int mpc_reset_stats(void);
 /* Per-kernel timing.  While enabled, each launch of a timed kernel is
  * bracketed by two CUDA events on its stream (no synchronisation).
  * mpc_profile_read() waits for those events and returns, for the kernel
- * `kernel` ("gemm_plain", "gemm_limb", "limb_planes", "private_relu",
- * "beaver_mul", "a2b"), the number of launches and their summed device time
+ * `kernel` ("gemm_plain", "gemm_plain_batched", "gemm_limb", "limb_planes",
+ * "batched_open", "private_relu", "private_relu_fused", "beaver_mul", "a2b"),
+ * the number of launches and their summed device time
  * since the last mpc_profile_reset().  Not for use inside stream capture. */
 int mpc_profile_enable(int on);
 int mpc_profile_reset(void);
@@ -291,27 +292,29 @@ typedef struct {
 
 /* Tuning of the batched call: products with M*N*K >= limb_min_macs run on the
  * limb engine (algo AUTO); persistent_ctas = CTAs of the persistent plain
- * kernel (0 = one per SM). */
+ * kernel, limb_ctas = CTAs of the persistent limb kernel (0 = one per SM). */
 typedef struct {
   double limb_min_macs;
   int persistent_ctas;
-  int reserved;
+  int limb_ctas;
 } mpc_tune;
 
-/* Fills the built-in tuning (limb from 2^28 ring MACs up). */
+/* Fills the built-in tuning (limb from 2^24 ring MACs up). */
 int mpc_tune_default(mpc_tune* out);
 
 /* Batched Beaver matmul (App. D.1.1 applied to many products at once): every
  * product is opened in one pass (one round for the whole batch), then the
  * products below the limb threshold run in one persistent launch of the plain
  * engine that hands out output tiles of any product from an atomic counter
- * (largest K first), and the others on the limb engine.  Results equal
+ * (largest K first), and the others in one persistent launch of the limb
+ * engine (after one digit-plane launch for all of them) that hands out 128 x
+ * 128 tiles of any product and party the same way.  Results equal
  * mpc_beaver_matmul on each product.  descs: host array of `count`
  * descriptors (read during the call only).  tune may be NULL (defaults).
  * ws: device workspace of mpc_matmul_batched_workspace_size() bytes (it holds
- * the work table, every product's opened E, F and B_0 + F, and limb
- * scratch).  Stream-capturable: the descriptors reach the device as kernel
- * parameters. */
+ * the work tables, every product's opened E, F and B_0 + F, and the digit
+ * planes of every limb product).  Stream-capturable: the descriptors and the
+ * limb engine's tensor maps reach the device as kernel parameters. */
 size_t mpc_matmul_batched_workspace_size(int P, int count, const mpc_matmul_desc* descs, int algo,
                                          const mpc_tune* tune);
 int mpc_beaver_matmul_batched(int P, int count, const mpc_matmul_desc* descs, int algo,
@@ -319,7 +322,8 @@ int mpc_beaver_matmul_batched(int P, int count, const mpc_matmul_desc* descs, in
                               void* stream);
 
 /* Autotuner: times the batched call (algo AUTO) for limb thresholds from
- * "never" down to 2^20 ring MACs and returns the fastest in *out.
+ * "never" through 2^32 .. 2^16 ring MACs to "always" and returns the fastest
+ * in *out.
  * Synchronises `stream`; not for use inside stream capture.  Writes Z. */
 int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int trunc_bits,
                          void* ws, size_t ws_bytes, void* stream, mpc_tune* out);

@@ -31,7 +31,7 @@ class MatmulDesc(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("limb_min_macs", ctypes.c_double), ("persistent_ctas", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("limb_ctas", ctypes.c_int)]
 
 
 _P = ctypes.POINTER

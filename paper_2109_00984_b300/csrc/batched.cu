@@ -1,13 +1,17 @@
 // Batched Beaver matmul: many products of uneven shapes in one call.
 //
-// Every product is opened in one batched kernel (one communication round for
-// the whole batch: all epsilons and deltas are revealed together, App. D.1.1),
-// then the products below the tuning threshold run in ONE persistent launch of
-// the plain engine, whose CTAs claim output tiles of any product from an
-// atomic counter (largest K first); products above it run on the tensor-core
-// limb engine.  The per-product descriptors reach the device through kernel
-// parameters (small table-writing kernels), so the whole call is
-// stream-capturable: a CUDA graph of it replays without host involvement.
+// All products are opened in the same round (one communication round for the
+// whole batch: all epsilons and deltas are revealed together, App. D.1.1).
+// The products below the tuned threshold are opened by one batched kernel and
+// run in ONE persistent launch of the plain engine, whose CTAs claim output
+// tiles of any product from an atomic counter (largest K first); the products
+// above it run in ONE persistent launch of the tensor-core limb engine, whose
+// CTAs likewise claim 128 x 128 tiles of any product and party, longest K
+// first, after one digit-plane launch that opens E and F while it cuts them
+// into digits.  The per-product descriptors reach the
+// device through kernel parameters (small table-writing kernels), so the
+// whole call is stream-capturable: a CUDA graph of it replays without host
+// involvement.
 #include <algorithm>
 #include <vector>
 
@@ -62,11 +66,32 @@ __global__ void __launch_bounds__(256) batched_open_kernel(const BatchProd* __re
 inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Plan {
-  std::vector<int> order;  // products in table order: plain ones (K descending), then limb
+  std::vector<int> order;  // products in table order: plain ones, then limb (each K descending)
   int n_plain = 0;
   size_t table_off = 0, efg_off = 0, limb_off = 0, total = 0;
   size_t limb_bytes = 0;
 };
+
+// The limb products of a plan as grouped-engine products (the grouped plane
+// pass opens their E and F itself).
+std::vector<GroupedProduct> grouped_of(const Plan& pl, const mpc_matmul_desc* descs) {
+  std::vector<GroupedProduct> g;
+  for (size_t j = pl.n_plain; j < pl.order.size(); ++j) {
+    const mpc_matmul_desc& d = descs[pl.order[j]];
+    GroupedProduct q{};
+    q.M = d.M;
+    q.N = d.N;
+    q.K = d.K;
+    q.X = (const u64*)d.X;
+    q.Y = (const u64*)d.Y;
+    q.A = (const u64*)d.A;
+    q.B = (const u64*)d.B;
+    q.C = (const u64*)d.C;
+    q.Z = (u64*)d.Z;
+    g.push_back(q);
+  }
+  return g;
+}
 
 bool use_limb(const mpc_matmul_desc& d, int algo, const mpc_tune& tune) {
   if (algo == MPC_ALGO_PLAIN) return false;
@@ -103,8 +128,9 @@ Plan make_plan(int P, int count, const mpc_matmul_desc* descs, int algo, const m
   Plan pl;
   std::vector<int> plain, limb;
   for (int i = 0; i < count; ++i) (use_limb(descs[i], algo, tune) ? limb : plain).push_back(i);
-  std::stable_sort(plain.begin(), plain.end(),
-                   [&](int a, int b) { return descs[a].K > descs[b].K; });
+  auto by_k = [&](int a, int b) { return descs[a].K > descs[b].K; };
+  std::stable_sort(plain.begin(), plain.end(), by_k);
+  std::stable_sort(limb.begin(), limb.end(), by_k);   // longest tiles first
   pl.order = plain;
   pl.order.insert(pl.order.end(), limb.begin(), limb.end());
   pl.n_plain = (int)plain.size();
@@ -112,14 +138,15 @@ Plan make_plan(int P, int count, const mpc_matmul_desc* descs, int algo, const m
   pl.table_off = off;
   off += al256((size_t)count * sizeof(BatchProd));
   pl.efg_off = off;
-  for (int i = 0; i < count; ++i) {
+  for (int i : plain) {  // opened E, F, G of the plain-engine products
     const mpc_matmul_desc& d = descs[i];
     off += al256((size_t)d.M * d.K * 8) + 2 * al256((size_t)d.K * d.N * 8);
   }
   pl.limb_off = off;
-  for (int i : limb)
-    pl.limb_bytes =
-        std::max(pl.limb_bytes, engine_ws(MPC_ALGO_LIMB, descs[i].M, descs[i].N, descs[i].K, 2, P));
+  if (!limb.empty()) {
+    const std::vector<GroupedProduct> g = grouped_of(pl, descs);
+    pl.limb_bytes = limb_grouped_workspace_bytes(P, (int)g.size(), g.data());
+  }
   pl.total = off + al256(pl.limb_bytes);
   return pl;
 }
@@ -161,19 +188,22 @@ int run_batched(int P, int count, const mpc_matmul_desc* descs, int algo, const 
     b.tiles = j < pl.n_plain ? (i64)P * tm * tn : 0;
     tile_base += b.tiles;
     b.open_base = open_base;
-    open_base += d.M * d.K + d.K * d.N;
     b.X = (const u64*)d.X;
     b.Y = (const u64*)d.Y;
     b.A = (const u64*)d.A;
     b.B = (const u64*)d.B;
     b.C = (const u64*)d.C;
     b.Z = (u64*)d.Z;
-    b.E = reinterpret_cast<u64*>(base + efg);
-    efg += al256((size_t)d.M * d.K * 8);
-    b.F = reinterpret_cast<u64*>(base + efg);
-    efg += al256((size_t)d.K * d.N * 8);
-    b.G = reinterpret_cast<u64*>(base + efg);
-    efg += al256((size_t)d.K * d.N * 8);
+    b.E = b.F = b.G = nullptr;
+    if (j < pl.n_plain) {  // the limb products are opened inside their plane pass
+      open_base += d.M * d.K + d.K * d.N;
+      b.E = reinterpret_cast<u64*>(base + efg);
+      efg += al256((size_t)d.M * d.K * 8);
+      b.F = reinterpret_cast<u64*>(base + efg);
+      efg += al256((size_t)d.K * d.N * 8);
+      b.G = reinterpret_cast<u64*>(base + efg);
+      efg += al256((size_t)d.K * d.N * 8);
+    }
   }
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(MPC_ECUDA, "counter reset: %s", cudaGetErrorString(e));
@@ -185,30 +215,21 @@ int run_batched(int P, int count, const mpc_matmul_desc* descs, int algo, const 
     table_write_kernel<<<1, kTablePerLaunch, 0, s>>>(ch, tbl);
     if (int rc = check_launch("batched table")) return rc;
   }
-  batched_open_kernel<<<grid_for(open_base, 256), 256, 0, s>>>(tbl, count, P, open_base);
-  if (int rc = check_launch("batched open")) return rc;
+  if (pl.n_plain > 0) {
+    KernelTimer timer("batched_open", s);
+    batched_open_kernel<<<grid_for(open_base, 256), 256, 0, s>>>(tbl, pl.n_plain, P, open_base);
+    if (int rc = check_launch("batched open")) return rc;
+  }
   if (pl.n_plain > 0) {
     const int ctas = tune.persistent_ctas > 0 ? tune.persistent_ctas : sm_count();
     if (int rc = launch_gemm_plain_batched(tbl, pl.n_plain, P, trunc_bits, counter, ctas, s))
       return rc;
   }
-  for (int j = pl.n_plain; j < count; ++j) {
-    const BatchProd& b = h[j];
-    GemmArgs g{};
-    g.M = b.M;
-    g.N = b.N;
-    g.K = b.K;
-    g.trunc_bits = trunc_bits;
-    g.njobs = P;
-    for (int p = 0; p < P; ++p) {
-      g.jobs[p].A1 = b.E;
-      g.jobs[p].B1 = p == 0 ? b.G : b.B + (i64)p * b.K * b.N;
-      g.jobs[p].A2 = b.A + (i64)p * b.M * b.K;
-      g.jobs[p].B2 = b.F;
-      g.jobs[p].C = b.C + (i64)p * b.M * b.N;
-      g.jobs[p].Z = b.Z + (i64)p * b.M * b.N;
-    }
-    if (int rc = run_gemm(g, MPC_ALGO_LIMB, base + pl.limb_off, pl.limb_bytes, s)) return rc;
+  if (pl.n_plain < count) {
+    const std::vector<GroupedProduct> g = grouped_of(pl, descs);
+    if (int rc = launch_gemm_limb_grouped(P, (int)g.size(), g.data(), trunc_bits, tune.limb_ctas,
+                                          base + pl.limb_off, pl.limb_bytes, s))
+      return rc;
   }
   uint64_t opened = 0, macs = 0;
   for (int i = 0; i < count; ++i) {
@@ -221,9 +242,9 @@ int run_batched(int P, int count, const mpc_matmul_desc* descs, int algo, const 
 
 mpc_tune default_tune() {
   mpc_tune t;
-  t.limb_min_macs = 268435456.0;  // 2^28 ring MACs per party-GEMM
+  t.limb_min_macs = 16777216.0;  // 2^24 ring MACs per party-GEMM
   t.persistent_ctas = 0;
-  t.reserved = 0;
+  t.limb_ctas = 0;
   return t;
 }
 
@@ -267,9 +288,11 @@ int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int tru
     return fail(MPC_ECUDA, "event creation failed");
   mpc_tune best = default_tune();
   float best_ms = -1.f;
-  // Candidate thresholds: everything plain, then 2^32 down to 2^20 ring MACs.
+  // Candidate thresholds: everything plain, 2^32 down to 2^16 ring MACs, and
+  // everything on the limb engine.
   std::vector<double> cands = {1e300};
-  for (int lg = 32; lg >= 20; lg -= 2) cands.push_back((double)(1ull << lg));
+  for (int lg = 32; lg >= 16; lg -= 2) cands.push_back((double)(1ull << lg));
+  cands.push_back(0.0);
   int rc = MPC_OK;
   for (double c : cands) {
     mpc_tune t = default_tune();

@@ -100,6 +100,24 @@ size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs);
 int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t s);
 bool limb_supported(i64 M, i64 N, i64 K);
 
+// Grouped limb engine: the Beaver products of a batch in one digit-plane launch
+// (which also opens E and F) and one persistent GEMM launch.  Per product and
+// party p:
+//   Z_p = trunc(C_p + E G_p + A_p F),  E = sum_q (X_q - A_q), F = sum_q (Y_q - B_q),
+//   G_0 = B_0 + F, G_p = B_p (p >= 1),
+// with X, A [P][M][K], Y, B [P][K][N], C and Z [P][M][N] (device).  Products
+// are processed in the order given: put the longest K first so that the
+// persistent CTAs finish together.
+struct GroupedProduct {
+  i64 M, N, K;
+  const u64 *X, *Y, *A, *B, *C;
+  u64* Z;
+};
+size_t limb_grouped_workspace_bytes(int P, int count, const GroupedProduct* prods);
+// ctas: persistent CTAs (0 = one per SM).
+int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int trunc_bits,
+                             int ctas, void* ws, size_t ws_bytes, cudaStream_t s);
+
 // Engine dispatch shared by the entry points: split choice, workspace bytes
 // (split-K partials, then limb planes) and the launch of one GEMM job set.
 int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);

@@ -53,14 +53,22 @@ def _to_dev(prods, P):
 
 
 @pytest.mark.parametrize("P", [2, 3])
-@pytest.mark.parametrize("mode", ["plain", "limb", "mixed"])
+@pytest.mark.parametrize("mode", ["plain", "limb", "mixed", "limb_3ctas", "limb_1cta"])
 def test_batched_matches_oracle(mpc, P, mode, rng):
+    """limb_3ctas / limb_1cta: the persistent limb kernel on 3 CTAs or 1, so
+    each CTA runs many tiles of products of different K back to back (the
+    barrier phases, chunk counts and TMEM slots carry over between tiles)."""
     dims, prods, refs = _small_batch(rng, P, 17)
     dprods = _to_dev(prods, P)
     tune = mpc.default_tune()
     if mode == "mixed":
         tune.limb_min_macs = float(np.median(dims.prod(1)))   # about half on each engine
-    algo = {"plain": mpc.PLAIN, "limb": mpc.LIMB, "mixed": mpc.AUTO}[mode]
+    if mode == "limb_3ctas":
+        tune.limb_ctas = 3
+    if mode == "limb_1cta":
+        tune.limb_ctas = 1
+    algo = {"plain": mpc.PLAIN, "limb": mpc.LIMB, "mixed": mpc.AUTO, "limb_3ctas": mpc.LIMB,
+            "limb_1cta": mpc.LIMB}[mode]
     mpc.beaver_matmul_batched(dprods, algo=algo, trunc_bits=16, tune=tune)
     mpc.sync_status()
     for i, (d, r) in enumerate(zip(dprods, refs)):
@@ -134,19 +142,30 @@ def test_uneven_512_batch_sampled(mpc):
         Z = torch.empty((P, M, N), dtype=torch.int64, device="cuda")
         hostXY.append((X, Y))
         dprods.append((dev(X), dev(Y), A, B, C, Z))
+    macs = dims.prod(1)
+    picks = sorted(set([int(np.argmin(macs)), int(np.argmax(macs))] +
+                       [int(i) for i in np.random.default_rng(4).choice(len(dims), 6, replace=False)]))
+
+    def check(label):
+        for i in picks:
+            M, N, K = (int(v) for v in dims[i])
+            r = np.random.default_rng(i)
+            rows = np.sort(r.choice(M, min(M, 24), replace=False))
+            cols = np.sort(r.choice(N, min(N, 24), replace=False))
+            X, Y = hostXY[i]
+            ref = _oracle_block(X, Y, P, M, N, K, 5000 + i, rows, cols)
+            got = host(dprods[i][5])[:, rows][:, :, cols]
+            assert np.array_equal(got, ref), f"{label}: product {i} dims {dims[i]}"
+
     bm = mpc.BatchedMatmul(dprods, algo=mpc.AUTO, trunc_bits=16)
     bm.autotune()
     bm()
     mpc.sync_status()
-    macs = dims.prod(1)
-    picks = sorted(set([int(np.argmin(macs)), int(np.argmax(macs))] +
-                       [int(i) for i in np.random.default_rng(4).choice(len(dims), 6, replace=False)]))
-    for i in picks:
-        M, N, K = (int(v) for v in dims[i])
-        r = np.random.default_rng(i)
-        rows = np.sort(r.choice(M, min(M, 24), replace=False))
-        cols = np.sort(r.choice(N, min(N, 24), replace=False))
-        X, Y = hostXY[i]
-        ref = _oracle_block(X, Y, P, M, N, K, 5000 + i, rows, cols)
-        got = host(dprods[i][5])[:, rows][:, :, cols]
-        assert np.array_equal(got, ref), f"product {i} dims {dims[i]}"
+    check("autotuned")
+    # every product on the persistent limb engine
+    for d in dprods:
+        d[5].fill_(-1)
+    bm = mpc.BatchedMatmul(dprods, algo=mpc.LIMB, trunc_bits=16)
+    bm()
+    mpc.sync_status()
+    check("all limb")
