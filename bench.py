@@ -58,6 +58,8 @@ def parse():
                          "batched: 512 uneven Beaver matmuls; elementwise: the HBM-bound "
                          "kernels at n = 2^20 .. 2^26")
     ap.add_argument("--sizes", default="1024,2048,4096,8192")
+    ap.add_argument("--elem-log2", default="20,22,24,26",
+                    help="elementwise workload: log2 of the element counts")
     return ap.parse_args()
 
 
@@ -1021,7 +1023,7 @@ def run_elementwise(args):
     peaks = load_peaks()
     clocks = ClockSampler(0)
     clocks.start()
-    res = extra_hbm_kernels(dev, peaks, [1 << e for e in range(20, 27, 2)],
+    res = extra_hbm_kernels(dev, peaks, [1 << int(e) for e in args.elem_log2.split(",")],
                             reps=max(3, args.steps))
     res["clocks"] = clocks.stop()
     print(json.dumps(res), flush=True)
