@@ -252,6 +252,20 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
                       const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
                       int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream);
 
+/* Beaver convolution followed by the fused private ReLU, two parties (§5.2
+ * "Comparators", App. D.1.1, D.1.4): the same result as
+ *   mpc_beaver_conv2d(2, d, X, W, A, B, C, Z, algo, trunc_bits, ws, ...) then
+ *   mpc_private_relu_fused(2, n, Z, Y, seed, relu_op, ...)
+ * bit for bit (material at relu_op .. relu_op + 3), with Y in place of Z.  When
+ * the convolution's GEMM is split along K, the ReLU kernel adds the partial
+ * sums, C and the truncation itself as it loads each element, instead of a
+ * separate reduction kernel writing Z first.  Y [2][batch][c_out][ho][wo]
+ * (device); ws as mpc_conv2d_workspace_size().  P must be 2. */
+int mpc_beaver_conv2d_relu(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                           const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Y,
+                           int algo, int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                           size_t ws_bytes, void* stream);
+
 /* Beaver matmul that allocates nothing (the paper has no counterpart: this is
  * an interface for callers that can neither allocate device memory when they
  * call the library nor hand it a workspace, e.g. a host program whose device

@@ -65,6 +65,8 @@ SIGNATURES = {
     "mpc_beaver_matmul_noalloc": (c_int, [c_int, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp,
                                           c_vp, c_int, c_vp]),
     "mpc_conv2d_workspace_size": (c_size, [c_int, _P(ConvDesc), c_int]),
+    "mpc_beaver_conv2d_relu": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                       c_int, c_int, c_u64, c_u64, c_vp, c_size, c_vp]),
     "mpc_beaver_conv2d": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int,
                                   c_int, c_vp, c_size, c_vp]),
     "mpc_tune_default": (c_int, [_P(Tune)]),

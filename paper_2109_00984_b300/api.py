@@ -225,6 +225,21 @@ def beaver_conv2d(X, W, A, B, C, d, algo=PLAIN, trunc_bits=0, out=None, ws=None)
     return Z
 
 
+def beaver_conv2d_relu(X, W, A, B, C, d, seed, relu_op, algo=PLAIN, trunc_bits=0, out=None,
+                       ws=None):
+    """Beaver convolution then the fused private ReLU (material at relu_op .. relu_op + 3),
+    two parties; equals beaver_conv2d followed by private_relu_fused."""
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Y = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), algo)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_relu(P, ctypes.byref(d), _ptr(X), _ptr(W), _ptr(A), _ptr(B),
+                                       _ptr(C), _ptr(Y), algo, trunc_bits, seed, relu_op,
+                                       _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return Y
+
+
 def conv2d_workspace_size(P, d, algo=PLAIN):
     return int(_L().mpc_conv2d_workspace_size(P, ctypes.byref(d), algo))
 

@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "host.hpp"
 #include "fused.cuh"
+#include "gemm.hpp"
 
 namespace mpc {
 
@@ -279,6 +280,53 @@ __global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u6
   }
 }
 
+// The fused ReLU of a two-party GEMM job set's output, reduced on the fly: x_p
+// of output index i = trunc(C_p[i] + sum_s partial[s][p][row][col]) with
+// (row, col) the GEMM position of i (inverse of gemm_out_index), or Z_p[i]
+// when the job set was not split.  Same grid and quad layout as
+// relu_fused_quad_kernel.
+__global__ void __launch_bounds__(256, 3) relu_gemm_quad_kernel(const GemmArgs g, u64* Y,
+                                                             u64 seed, u64 op) {
+  const i64 n = g.M * g.N;
+  const i64 stride = (i64)gridDim.x * blockDim.x;
+  const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
+  const int j = threadIdx.x & 3;
+  const i64 sstride = (i64)g.njobs * n;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < npad; i += stride) {
+    const bool valid = i < n;
+    Sh2 x{{0ull, 0ull}};
+    if (valid) {
+      if (g.splits > 1) {
+        i64 row, col;
+        if (g.hw_out) {  // i = (b M + row) hw + pos, col = b hw + pos
+          const i64 q = i / g.hw_out, pos = i - q * g.hw_out;
+          const i64 b = q / g.M;
+          row = q - b * g.M;
+          col = b * g.hw_out + pos;
+        } else {
+          row = i / g.N;
+          col = i - row * g.N;
+        }
+        const u64* part = g.partial + row * g.N + col;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          u64 acc = g.jobs[p].C ? g.jobs[p].C[i] : 0ull;
+          for (int sp = 0; sp < g.splits; ++sp) acc += part[sp * sstride + p * n];
+          x.v[p] = g.trunc_bits > 0 ? sar(acc, g.trunc_bits) : acc;
+        }
+      } else {
+        x.v[0] = g.jobs[0].Z[i];
+        x.v[1] = g.jobs[1].Z[i];
+      }
+    }
+    const Sh2 y = relu_quad(x, seed, op, i >> 2, j);
+    if (valid) {
+      Y[i] = y.v[0];
+      Y[n + i] = y.v[1];
+    }
+  }
+}
+
 // ---- any number of parties: a tree of adders (one element per thread) ---------------
 // Adders are numbered level by level, left to right; adder a uses gates 12a..12a+11
 // of T [12 (P-1)][3][P][n].
@@ -486,6 +534,20 @@ inline uint64_t a2b_rounds(int P) {
   }
 
 }  // namespace
+
+int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s) {
+  if (g.njobs != 2) return fail(MPC_EUNSUPPORTED, "fused ReLU of a GEMM needs two parties");
+  const i64 n = g.M * g.N;
+  if (n == 0) return MPC_OK;
+  {
+    KernelTimer timer("private_relu_fused", s);
+    relu_gemm_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, s>>>(g, Y, seed, op);
+    if (int rc = check_launch("private_relu_fused (of a GEMM)")) return rc;
+  }
+  stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,
+            (uint64_t)MPC_KS_GATES * n, (uint64_t)MPC_KS_GATES * 6ull * n + 2ull * n + 6ull * n, 0);
+  return MPC_OK;
+}
 
 }  // namespace mpc
 

@@ -44,6 +44,9 @@ struct GemmArgs {
   int trunc_bits;
   int njobs;
   int splits;
+  // With split-K, leave the raw partial sums in `partial` for the caller to
+  // reduce (launch_relu_from_partials) instead of running gemm_reduce.
+  int defer_reduce;
   u64* partial;
   const ConvGather* gather;  // host pointer; when set, B1/B2 are implicit im2col (limb only)
   GemmJob jobs[MPC_MAX_PARTIES];
@@ -122,6 +125,15 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
 // (split-K partials, then limb planes) and the launch of one GEMM job set.
 int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
 size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
-int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s);
+// used (optional): the job set as launched (split count, partial buffer).
+int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s,
+             GemmArgs* used = nullptr);
+
+// Two-party fused private ReLU (dealer regenerated in registers, material at op
+// .. op + 3, as mpc_private_relu_fused) of a GEMM job set's output without
+// materialising it: element i of party p is trunc(C_p[i] + sum over splits of
+// the partial sums at the GEMM position of output index i), or Z_p[i] when
+// the job set was not split.  Y [2][M N] receives the ReLU.  Requires njobs = 2.
+int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s);
 
 }  // namespace mpc

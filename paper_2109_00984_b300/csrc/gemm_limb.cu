@@ -1162,6 +1162,51 @@ __device__ __forceinline__ void planes_b_tile(uint32_t* tile, const Src& src, __
   store_b_tile(tile, out, (int)N, (int)Kp, (int)n0, (int)k0);
 }
 
+// B side with two outputs from one read of the source: the planes of the
+// element v to `out`, and those of v + add (add[k][n], row-major like the
+// source) to `out2` (F and G = B_0 + F of a Beaver product).  Padding stays 0
+// in both.
+template <class Src>
+__device__ __forceinline__ void planes_b_tile2(uint32_t* tile, const Src& src, const u64* add,
+                                               __nv_bfloat16* out, __nv_bfloat16* out2, i64 N,
+                                               i64 K, i64 Kp, int bx, int by) {
+  const i64 k0 = (i64)bx * PB_TK, n0 = (i64)by * PB_TN;
+  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
+  const i64 n = n0 + nl;
+  u64 v[4][2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int kl = 2 * (kq + 8 * j);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const i64 k = k0 + kl + e;
+      v[j][e] = (n < N && k < K) ? src(k * N + n) : 0ull;
+    }
+    const u64 u0 = digit_base(v[j][0]), u1 = digit_base(v[j][1]);
+#pragma unroll
+    for (int pl = 0; pl < 8; ++pl)
+      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+  }
+  __syncthreads();
+  store_b_tile(tile, out, (int)N, (int)Kp, (int)n0, (int)k0);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int kl = 2 * (kq + 8 * j);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const i64 k = k0 + kl + e;
+      if (n < N && k < K) v[j][e] += add[k * N + n];
+    }
+    const u64 u0 = digit_base(v[j][0]), u1 = digit_base(v[j][1]);
+#pragma unroll
+    for (int pl = 0; pl < 8; ++pl)
+      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+  }
+  __syncthreads();
+  store_b_tile(tile, out2, (int)N, (int)Kp, (int)n0, (int)k0);
+}
+
 // B side of a convolution, gathered straight from the data (implicit im2col):
 // the same tiling and stores as planes_b_tile, with element (k, n) read at its
 // data position instead of from a materialised im2col matrix.  z = 0 writes
@@ -1269,12 +1314,15 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
 // source (A side [rows][K] or B side [K][rows], row-major u64) with its plane
 // buffer; block b belongs to the last task whose block_base <= b.  With
 // nparty > 0 the source is opened on the fly: element i is
-// sum_p (src[p][i] - sub[p][i]) (+ add[i]), party p at p * pstride.
+// sum_p (src[p][i] - sub[p][i]) (+ add[i]), party p at p * pstride.  A B-side
+// task with out2 also writes the planes of that element plus add2[i] to out2.
 struct __align__(16) PlaneTask {
   const u64* src;
   const u64* sub;
   const u64* add;
+  const u64* add2;
   __nv_bfloat16* out;
+  __nv_bfloat16* out2;
   i64 rows, K, Kp;
   i64 block_base;
   i64 pstride;
@@ -1305,6 +1353,9 @@ __global__ void __launch_bounds__(256) limb_planes_grouped(const PlaneTask* __re
     const OpenedSrc src{t.src, t.sub, t.add, t.pstride, t.nparty};
     if (t.side == 0)
       planes_a_part(src, t.out, t.rows, t.K, t.Kp, local, t.nblk);
+    else if (t.out2)
+      planes_b_tile2(tile, src, t.add2, t.out, t.out2, t.rows, t.K, t.Kp, (int)(local % t.bx),
+                     (int)(local / t.bx));
     else
       planes_b_tile(tile, src, t.out, t.rows, t.K, t.Kp, (int)(local % t.bx), (int)(local / t.bx));
   }
@@ -1523,7 +1574,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
     if (int rc = check_launch("gemm_limb")) return rc;
   }
-  return g.splits > 1 ? gemm_reduce(g, s) : MPC_OK;
+  return (g.splits > 1 && !g.defer_reduce) ? gemm_reduce(g, s) : MPC_OK;
 }
 
 namespace {
@@ -1605,11 +1656,21 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
     const i64 K1p = pair_k(g.K);
     const size_t a_bytes = al256((size_t)16 * g.M * K1p), b_bytes = al256((size_t)16 * g.N * K1p);
     // Sources in map order: A side E, A_0..A_{P-1}; B side G, B_1..B_{P-1},
-    // F.  E = sum_p (X_p - A_p), F = sum_p (Y_p - B_p) and G = B_0 + F are
-    // opened inside the plane pass.
+    // F.  E = sum_p (X_p - A_p) and F = sum_p (Y_p - B_p) are opened inside
+    // the plane pass; one task writes both F and G = B_0 + F.
     const i64 mk = g.M * g.K, kn = g.K * g.N;
+    __nv_bfloat16* g_planes = nullptr;
     for (int m = 0; m < nmaps; ++m) {
       const bool aside = m <= P;
+      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(planes);
+      planes += aside ? a_bytes : b_bytes;
+      const i64 rows = aside ? g.M : g.N;
+      if (int rc = encode_planes(&hm[(size_t)i * nmaps + m], out, rows, K1p, aside ? BM : BN))
+        return rc;
+      if (m == P + 1) {  // G: written by F's task
+        g_planes = out;
+        continue;
+      }
       PlaneTask t{};
       if (m == 0) {
         t.src = g.X;
@@ -1618,20 +1679,16 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
         t.nparty = P;
       } else if (aside) {
         t.src = g.A + (i64)(m - 1) * mk;
-      } else if (m == P + 1 || m == 2 * P + 1) {
+      } else if (m == 2 * P + 1) {
         t.src = g.Y;
         t.sub = g.B;
-        t.add = m == P + 1 ? g.B : nullptr;   // G = B_0 + F
         t.pstride = kn;
         t.nparty = P;
+        t.add2 = g.B;      // party 0's B: G = B_0 + F
+        t.out2 = g_planes;
       } else {
         t.src = g.B + (i64)(m - P - 1) * kn;
       }
-      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(planes);
-      planes += aside ? a_bytes : b_bytes;
-      const i64 rows = aside ? g.M : g.N;
-      if (int rc = encode_planes(&hm[(size_t)i * nmaps + m], out, rows, K1p, aside ? BM : BN))
-        return rc;
       t.out = out;
       t.rows = rows;
       t.K = g.K;

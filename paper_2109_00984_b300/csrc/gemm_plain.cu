@@ -215,7 +215,7 @@ int launch_gemm_plain(const GemmArgs& g_in, cudaStream_t s) {
     gemm_plain_kernel<<<grid, kThreads, 0, s>>>(g);
     if (int rc = check_launch("gemm_plain")) return rc;
   }
-  return g.splits > 1 ? gemm_reduce(g, s) : MPC_OK;
+  return (g.splits > 1 && !g.defer_reduce) ? gemm_reduce(g, s) : MPC_OK;
 }
 
 }  // namespace mpc

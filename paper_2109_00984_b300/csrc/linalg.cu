@@ -195,13 +195,14 @@ size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
   return b;
 }
 
-int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s) {
+int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s, GemmArgs* used) {
   if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
   const int npairs = g.jobs[0].A2 ? 2 : 1;
   g.splits = engine_splits(algo, g.M, g.N, g.K, npairs, g.njobs);
   const size_t pb = align256(partial_bytes(g.splits, g.njobs, g.M, g.N));
   if (ws_bytes < pb) return fail(MPC_ENOMEM, "engine workspace too small for split-K partials");
   g.partial = g.splits > 1 ? static_cast<u64*>(ws) : nullptr;
+  if (used) *used = g;
   void* rest = static_cast<char*>(ws) + pb;
   if (algo == MPC_ALGO_LIMB) return launch_gemm_limb(g, rest, ws_bytes - pb, s);
   return launch_gemm_plain(g, s);
@@ -326,9 +327,17 @@ size_t mpc_conv2d_workspace_size(int P, const mpc_conv_desc* d, int algo) {
   return conv_ws(P, *d, ho, wo, resolve_algo(algo, M, N, K));
 }
 
-int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
-                      const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
-                      int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream) {
+}  // extern "C"
+
+namespace mpc {
+namespace {
+
+// The Beaver convolution; with `deferred`, a split-K job set leaves its partial
+// sums for the caller (the job set as launched is copied there).
+int beaver_conv2d_impl(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                       const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
+                       int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream,
+                       GemmArgs* deferred) {
   MPC_CHECK_PARTIES(P);
   if (int rc = check_algo(algo)) return rc;
   i64 ho, wo;
@@ -385,6 +394,7 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
   g.trunc_bits = trunc_bits;
   g.njobs = P;
   g.gather = gather ? &cg : nullptr;
+  g.defer_reduce = deferred != nullptr;
   for (int p = 0; p < P; ++p) {
     g.jobs[p].A1 = p == 0 ? G : (const u64*)B + (i64)p * M * K;
     g.jobs[p].B1 = Ecol;
@@ -393,11 +403,38 @@ int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const ui
     g.jobs[p].C = (const u64*)C + (i64)p * M * N;
     g.jobs[p].Z = (u64*)Z + (i64)p * M * N;
   }
-  int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s);
+  int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, deferred);
   if (rc == MPC_OK)
     stats_add(1, 8ull * (uint64_t)(nx + M * K), 0, (uint64_t)P * (nx + M * K + M * N),
               (uint64_t)P * 2ull * M * N * K);
   return rc;
+}
+
+}  // namespace
+}  // namespace mpc
+
+extern "C" {
+
+int mpc_beaver_conv2d(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                      const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
+                      int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream) {
+  return beaver_conv2d_impl(P, d, X, W, A, B, C, Z, algo, trunc_bits, ws, ws_bytes, stream,
+                            nullptr);
+}
+
+int mpc_beaver_conv2d_relu(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
+                           const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Y,
+                           int algo, int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "convolution + fused ReLU supports P = 2 (got %d)", P);
+  GemmArgs used{};
+  used.njobs = 0;
+  if (int rc = beaver_conv2d_impl(P, d, X, W, A, B, C, Y, algo, trunc_bits, ws, ws_bytes, stream,
+                                  &used))
+    return rc;
+  if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
+  return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
 }
 
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo) {

@@ -166,14 +166,18 @@ class PrivateConv1dStack:
                                       out=(t["A"], t["B"], t["C"]), ws=self.ws)
             elif wait_dealer and self.ready[slot][l] is not None:
                 main.wait_event(self.ready[slot][l])
-            api.beaver_conv2d(X, self.W[l], t["A"], t["B"], t["C"], d, self.algo,
-                              trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)
             n = b["n"]
             if self.fused_relu:
                 assert (ops["b2a"], ops["mul"], ops["relu"]) == (ops["and"] + 1, ops["and"] + 2,
                                                                  ops["and"] + 3)
-                api.private_relu_fused(b["Z"], seed, ops["and"], out=b["Y"])
+                # convolution + truncation + ReLU: the ReLU kernel reduces the
+                # GEMM's split-K partial sums itself
+                api.beaver_conv2d_relu(X, self.W[l], t["A"], t["B"], t["C"], d, seed, ops["and"],
+                                       self.algo, trunc_bits=self.frac_bits, out=b["Y"],
+                                       ws=self.ws)
             else:
+                api.beaver_conv2d(X, self.W[l], t["A"], t["B"], t["C"], d, self.algo,
+                                  trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)
                 api.ttp_and_triples(self.P, n, seed, ops["and"], out=b["T"])
                 api.ttp_b2a_bits(self.P, n, seed, ops["b2a"], out=(b["ra"], b["rb"]))
                 MT = b["MT"]

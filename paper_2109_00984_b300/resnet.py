@@ -127,6 +127,24 @@ class PrivateResNet18:
         ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d(X, Wsh, A, B, C, d, self.algo, self.frac_bits, ws=ws)
 
+    def conv_relu(self, X, Wsh, stride, pad, op, relu_op, key=None):
+        """A convolution whose output goes straight into a ReLU: one composite call
+        (the ReLU kernel reduces the GEMM's split-K partial sums itself)."""
+        if not self.fused_relu:
+            return self.relu(self.conv(X, Wsh, stride, pad, op, key), relu_op)
+        P, N, Cin, H, W = X.shape
+        Cout, _, k, _ = Wsh.shape[1:]
+        d = api.conv_desc(N, Cin, H, W, Cout, k, k, stride, stride, pad, pad)
+        trip = self._triple(key) if key is not None else None
+        if trip is None:
+            ws = self._ws(max(api.conv2d_workspace_size(P, d, self.algo),
+                              api.conv2d_triple_workspace_size(P, d, self.algo)))
+            trip = self._deal_conv(d, op, ws)
+        A, B, C = trip
+        ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
+        return api.beaver_conv2d_relu(X, Wsh, A, B, C, d, self.seed, relu_op, self.algo,
+                                      self.frac_bits, ws=ws)
+
     def relu(self, X, op):
         P = X.shape[0]
         flat = X.reshape(P, -1)
@@ -191,19 +209,28 @@ class PrivateResNet18:
     def _online(self, x, schedule):
         ops = schedule["ops"]
         X = api.ring_share(x, self.P, 0, self.seed, ops["input"], self.frac_bits)
-        for layer in self.layers:
+        fused_next = False
+        for li, layer in enumerate(self.layers):
             kind, name = layer[0], layer[1]
             if kind == "conv":
-                X = self.conv(X, self.W[name], layer[5], layer[6], ops[name], name)
+                nxt = self.layers[li + 1] if li + 1 < len(self.layers) else None
+                if nxt is not None and nxt[0] == "relu":   # conv then ReLU: one call
+                    X = self.conv_relu(X, self.W[name], layer[5], layer[6], ops[name],
+                                       ops[nxt[1]], name)
+                    fused_next = True
+                else:
+                    X = self.conv(X, self.W[name], layer[5], layer[6], ops[name], name)
             elif kind == "relu":
-                X = self.relu(X, ops[name])
+                if not fused_next:
+                    X = self.relu(X, ops[name])
+                fused_next = False
             elif kind == "maxpool":
                 X = self.maxpool(X, layer[2], layer[3], layer[4],
                                  [ops[f"{name}.{l}"] for l in range(4)])
             elif kind == "block":
                 _, name, cin, cout, s = layer
-                Y = self.conv(X, self.W[name + ".conv1"], s, 1, ops[name + ".conv1"], name + ".conv1")
-                Y = self.relu(Y, ops[name + ".relu1"])
+                Y = self.conv_relu(X, self.W[name + ".conv1"], s, 1, ops[name + ".conv1"],
+                                   ops[name + ".relu1"], name + ".conv1")
                 Y = self.conv(Y, self.W[name + ".conv2"], 1, 1, ops[name + ".conv2"], name + ".conv2")
                 if s != 1 or cin != cout:
                     S = self.conv(X, self.W[name + ".down"], s, 0, ops[name + ".down"],

@@ -1,0 +1,74 @@
+"""Beaver convolution + fused private ReLU in one call (mpc_beaver_conv2d_relu).
+
+The composite must equal, word for word, the oracle's Beaver convolution with
+truncation followed by its private ReLU on the dealer material at
+op .. op + 3, on both engines, for geometries whose GEMM is split along K (the
+ReLU kernel then reduces the partial sums, adds C and truncates itself; batch
+2 checks the NCHW scatter) and ones that are not split.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import dev, host  # noqa: E402
+
+from oracle import beaver, binary, dealer, truncation  # noqa: E402
+
+SEED = 1
+
+GEOMS = [
+    # (batch, c_in, h, w, c_out, k_h, k_w, stride, pad_h, pad_w)
+    (1, 64, 1, 200, 24, 1, 7, 1, 0, 3),     # 1-D, split-K on both engines
+    (2, 32, 12, 12, 40, 3, 3, 1, 1, 1),     # batch 2 (output scatter), split-K
+    (1, 4, 20, 20, 130, 3, 3, 2, 1, 1),     # short K: not split, ragged rows
+]
+
+
+@pytest.fixture(scope="module")
+def mpc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_00984_b300 as m
+    return m
+
+
+@pytest.mark.parametrize("geom", GEOMS)
+@pytest.mark.parametrize("engine", ["plain", "limb"])
+def test_conv2d_relu_matches_oracle(mpc, geom, engine, rng):
+    b, ci, h, w, co, kh, kw, st, ph, pw = geom
+    P = 2
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 90, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    n = Z[0].size
+    op = 400
+    T = dealer.and_triples(P, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(P, n, SEED, op + 1)
+    mt = dealer.mul_triple(P, n, SEED, op + 2)
+    ref = binary.private_relu(Z.reshape(P, n), T, ra, rb, mt, SEED, op + 3).reshape(Z.shape)
+
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    algo = mpc.LIMB if engine == "limb" else mpc.PLAIN
+    Y = mpc.beaver_conv2d_relu(dev(X), dev(W), dev(A), dev(B), dev(C), d, SEED, op, algo=algo,
+                               trunc_bits=16)
+    mpc.sync_status()
+    assert np.array_equal(host(Y), ref)
+    # the two separate calls give the same words
+    Z2 = mpc.beaver_conv2d(dev(X), dev(W), dev(A), dev(B), dev(C), d, algo=algo, trunc_bits=16)
+    Y2 = mpc.private_relu_fused(Z2.reshape(P, n), SEED, op).reshape(Y.shape)
+    assert torch.equal(Y, Y2)
+
+
+def test_conv2d_relu_rejects_other_party_counts(mpc):
+    from paper_2109_00984_b300 import _lib
+    import ctypes
+    lib = _lib.load()
+    d = mpc.conv_desc(1, 4, 1, 16, 8, 1, 3, 1, 0, 1)
+    fake = ctypes.c_void_p(0x1000)
+    rc = lib.mpc_beaver_conv2d_relu(3, ctypes.byref(d), fake, fake, fake, fake, fake, fake, 0, 16,
+                                    1, 1, fake, 1 << 20, None)
+    assert rc == -6
