@@ -1101,182 +1101,92 @@ __device__ __forceinline__ void planes_a_part(const Src& src, __nv_bfloat16* out
   }
 }
 
-// B side: X is [K][N] row-major; planes are written transposed, by rows of N.
-// One CTA per tile of 64 k' x 32 n: coalesced row reads of X, digits into a
-// shared-memory tile [plane][n][k'] (33-word rows: the transposed stores hit
-// distinct banks), then each warp instruction writes 512 contiguous bytes of
-// one row's interleaved planes.
-constexpr int PB_TK = 64, PB_TN = 32, PB_ROW = PB_TK / 2 + 1;  // words per smem row
-constexpr int PB_PLANE = PB_TN * PB_ROW;                       // words per tile plane
-constexpr int PB_WORDS = NPLANE * PB_PLANE + 20;
-
-// Word index of (plane p, column n, word w) in the tile.  Plane p is skewed by
-// (p % 4) + 16 (p / 4) words so that the store phase, whose lanes read planes
-// 0..7 at word offsets {0, 4, 8, 12}, touches 32 distinct banks.
-__device__ __forceinline__ int pb_word(int p, int n, int w) {
-  return p * PB_PLANE + (p & 3) + 16 * (p >> 2) + n * PB_ROW + w;
-}
-
-// Store phase of the B-side plane tiles: the tile holds 64 k (32 words of two
-// bf16), i.e. four sub-steps, for 32 columns n; in the interleaved layout
-// those are 1024 contiguous bytes per column.  Lane l of a warp instruction
-// writes 16 bytes: sub-step (l / 16) + 2 h, plane (l / 2) % 8, k half l % 2.
-// Kp is a multiple of 16, so a sub-step never straddles the end.
-__device__ __forceinline__ void store_b_tile(const uint32_t* tile, __nv_bfloat16* out, int N,
-                                             int Kp, int n0, int k0) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int pl = (lane >> 1) & 7, half = lane & 1;
-  for (int idx = warp; idx < 2 * PB_TN; idx += 8) {
-    const int row = idx >> 1, tl = (lane >> 4) + 2 * (idx & 1);
-    const int nn = n0 + row, kk = k0 + KS * tl;
-    if (nn < N && kk < Kp) {
-      const int w4 = pb_word(pl, row, 8 * tl + 4 * half);
-      const uint4 v = make_uint4(tile[w4], tile[w4 + 1], tile[w4 + 2], tile[w4 + 3]);
-      *reinterpret_cast<uint4*>(out + plane_index(pl, nn, Kp, kk + 8 * half)) = v;
-    }
-  }
-}
-
+// B side from a row-major [K][N] source, K-major like the convolution gather
+// below: lane l of warp w owns column n = 16 by + l / 2 and the 8 consecutive
+// k of half l % 2 of sub-step t = 8 bx + w, reads them (16 consecutive n per
+// warp and k: whole 128-byte lines) and writes its digits straight into the
+// planes, one 16-byte store per plane.  With add (dual), the planes of v + add
+// go to out2 as well (F and G = B_0 + F of a Beaver product).
 template <class Src>
-__device__ __forceinline__ void planes_b_tile(uint32_t* tile, const Src& src, __nv_bfloat16* out,
-                                              i64 N, i64 K, i64 Kp, int bx, int by) {
-  const i64 k0 = (i64)bx * PB_TK, n0 = (i64)by * PB_TN;
-  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
-  const i64 n = n0 + nl;
-  // Load + digit phase: thread (nl, kq) owns k' pairs 2 (kq + 8 j), j = 0..3.
+__device__ __forceinline__ void planes_b_kmajor(const Src& src, const u64* add,
+                                                __nv_bfloat16* out, __nv_bfloat16* out2, i64 N,
+                                                i64 K, i64 Kp, int bx, int by) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const i64 t = (i64)bx * 8 + w;
+  const i64 n = (i64)by * 16 + (l >> 1);
+  if (t >= Kp / KS || n >= N) return;
+  const i64 k0 = t * KS + (l & 1) * 8;
+  u64 v[8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int kl = 2 * (kq + 8 * j);
-    u64 v[2];
+  for (int e = 0; e < 8; ++e) v[e] = k0 + e < K ? src((k0 + e) * N + n) : 0ull;
+  write_planes(v, out, n, Kp, k0);
+  if (out2) {
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const i64 k = k0 + kl + e;
-      v[e] = (n < N && k < K) ? src(k * N + n) : 0ull;
-    }
-    const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
-#pragma unroll
-    for (int pl = 0; pl < 8; ++pl)
-      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+    for (int e = 0; e < 8; ++e)
+      if (k0 + e < K) v[e] += add[(k0 + e) * N + n];
+    write_planes(v, out2, n, Kp, k0);
   }
-  __syncthreads();
-  store_b_tile(tile, out, (int)N, (int)Kp, (int)n0, (int)k0);
 }
 
-// B side with two outputs from one read of the source: the planes of the
-// element v to `out`, and those of v + add (add[k][n], row-major like the
-// source) to `out2` (F and G = B_0 + F of a Beaver product).  Padding stays 0
-// in both.
-template <class Src>
-__device__ __forceinline__ void planes_b_tile2(uint32_t* tile, const Src& src, const u64* add,
-                                               __nv_bfloat16* out, __nv_bfloat16* out2, i64 N,
-                                               i64 K, i64 Kp, int bx, int by) {
-  const i64 k0 = (i64)bx * PB_TK, n0 = (i64)by * PB_TN;
-  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;  // kq: 0..7
-  const i64 n = n0 + nl;
-  u64 v[4][2];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int kl = 2 * (kq + 8 * j);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const i64 k = k0 + kl + e;
-      v[j][e] = (n < N && k < K) ? src(k * N + n) : 0ull;
-    }
-    const u64 u0 = digit_base(v[j][0]), u1 = digit_base(v[j][1]);
-#pragma unroll
-    for (int pl = 0; pl < 8; ++pl)
-      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
-  }
-  __syncthreads();
-  store_b_tile(tile, out, (int)N, (int)Kp, (int)n0, (int)k0);
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int kl = 2 * (kq + 8 * j);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const i64 k = k0 + kl + e;
-      if (n < N && k < K) v[j][e] += add[k * N + n];
-    }
-    const u64 u0 = digit_base(v[j][0]), u1 = digit_base(v[j][1]);
-#pragma unroll
-    for (int pl = 0; pl < 8; ++pl)
-      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
-  }
-  __syncthreads();
-  store_b_tile(tile, out2, (int)N, (int)Kp, (int)n0, (int)k0);
-}
-
-// B side of a convolution, gathered straight from the data (implicit im2col):
-// the same tiling and stores as planes_b_tile, with element (k, n) read at its
-// data position instead of from a materialised im2col matrix.  z = 0 writes
-// pair 1 (the opened sum over src1 - sub1, shared by all jobs) to
-// outs.j[0].out; z = 1 + j writes job j's pair 2 (src2[j]) to outs.j[1 + j].out.  The CTA's 64 k are decoded once into a shared tap table
-// (offset ci h w + r w + s, r, s); column n = (b, oh, ow) is decoded once per
-// thread, so an element costs two bounds checks and an add.
-__device__ __forceinline__ void planes_b_conv_tile(uint32_t* tile, int* tap_off, int* tap_r,
-                                                   int* tap_s, const ConvGather& cg,
-                                                   const PlaneJobs& outs, int N, int K, int Kp,
-                                                   int bx, int by, int z) {
+// B side of a convolution, gathered straight from the data (implicit im2col),
+// K-major: lane l of warp w owns output column n = 16 by + l / 2 and the 8
+// consecutive k of half l % 2 of sub-step t = 8 bx + w, so that it writes its
+// digits straight into the planes ([n][Kp / 16][8][16]: one 16-byte store per
+// plane, the lane pair filling whole 32-byte sectors) with no shared-memory
+// transpose, and the 16 columns of a warp read 16 consecutive data positions
+// per k.  Output z: z = 0 is pair 1, the opened sum over src1 - sub1 (shared
+// by all jobs), written to outs.j[0]; z = 1 + j is job j's pair 2, src2[j],
+// written to outs.j[1 + j].  Each output has blocks of its own: one gather
+// feeding all of them (80 registers for three) ran at half the occupancy and
+// made the speech step 2 % slower.
+__device__ __forceinline__ void planes_b_conv_kmajor(const ConvGather& cg, const PlaneJobs& outs,
+                                                     int N, int K, int Kp, int bx, int by, int z) {
   const mpc_conv_desc& d = cg.d;
-  const int H = (int)d.h, W = (int)d.w;
-  const u64* src2 = z > 0 ? cg.src2[z - 1] : nullptr;
-  __nv_bfloat16* out = outs.j[z].out;
-  const int k0 = bx * PB_TK, n0 = by * PB_TN;
-  const int tid = threadIdx.x, nl = tid & 31, kq = tid >> 5;
-  if (tid < PB_TK) {
-    const int k = k0 + tid;
-    if (k >= K) {  // an out-of-range row offset makes every bounds check fail
-      tap_off[tid] = 0;
-      tap_r[tid] = -(1 << 30);
-      tap_s[tid] = 0;
-    } else {
-      const int kw = (int)d.kw, kh = (int)d.kh;
-      const int s_ = k % kw, r = (k / kw) % kh, ci = k / (kw * kh);
-      tap_off[tid] = (ci * H + r) * W + s_;
-      tap_r[tid] = r;
-      tap_s[tid] = s_;
-    }
-  }
-  // Output column n -> (b, oh, ow), and the data offset of its window origin
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int t = bx * 8 + w;
+  const int n = by * 16 + (l >> 1);
+  if (t >= Kp / KS || n >= N) return;
+  const int k0 = t * KS + (l & 1) * 8;
+  const int H = (int)d.h, W = (int)d.w, kh = (int)d.kh, kw = (int)d.kw;
+  // Output column n -> (b, oh, ow) and the data offset of its window origin
   // (32-bit: the host checks that every data offset fits).
-  const int n = n0 + nl;
-  const bool n_ok = n < N;
   const int wo = (int)cg.wo, ho = (int)cg.ho;
   const int ow = n % wo, tq = n / wo, oh = tq % ho, b = tq / ho;
   const int oy = oh * (int)d.stride_h - (int)d.pad_h, ox = ow * (int)d.stride_w - (int)d.pad_w;
   const int base = (b * (int)d.c_in * H + oy) * W + ox;
-  __syncthreads();
+  // Tap (ci, r, s) of k0, advanced per k.
+  const int khw = kh * kw;
+  int ci = k0 / khw;
+  int r = (k0 - ci * khw) / kw;
+  int sx = k0 - ci * khw - r * kw;
+  const u64* src2 = z > 0 ? cg.src2[z - 1] : nullptr;
+  u64 v[8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int kl = 2 * (kq + 8 * j);
-    u64 v[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int t = kl + e;
-      v[e] = 0;
-      const int y = oy + tap_r[t], x = ox + tap_s[t];
-      if (n_ok && (unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) {
-        const int off = base + tap_off[t];
-        if (z == 0) {
-          u64 acc = 0;
-          for (int q = 0; q < cg.n1; ++q) {
-            acc += cg.src1[q * cg.stride1 + off];
-            if (cg.sub1) acc -= cg.sub1[q * cg.stride1 + off];
-          }
-          v[e] = acc;
-        } else {
-          v[e] = src2[off];
+  for (int e = 0; e < 8; ++e) {
+    const int y = oy + r, x = ox + sx;
+    v[e] = 0;
+    if (k0 + e < K && (unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) {
+      const int off = base + (ci * H + r) * W + sx;
+      if (z == 0) {
+        u64 acc = 0;
+        for (int q = 0; q < cg.n1; ++q) {
+          acc += cg.src1[q * cg.stride1 + off];
+          if (cg.sub1) acc -= cg.sub1[q * cg.stride1 + off];
         }
+        v[e] = acc;
+      } else {
+        v[e] = src2[off];
       }
     }
-    const u64 u0 = digit_base(v[0]), u1 = digit_base(v[1]);
-#pragma unroll
-    for (int pl = 0; pl < 8; ++pl)
-      tile[pb_word(pl, nl, kl >> 1)] = pack_hi16(digit_bits(u0, pl), digit_bits(u1, pl));
+    if (++sx == kw) {
+      sx = 0;
+      if (++r == kh) {
+        r = 0;
+        ++ci;
+      }
+    }
   }
-  __syncthreads();
-  store_b_tile(tile, out, N, Kp, n0, k0);
+  write_planes(v, outs.j[z].out, n, Kp, k0);
 }
 
 // One launch for both plane sides of a GEMM: blocks [0, na * a_blk) cut the A
@@ -1290,10 +1200,10 @@ struct PlanesLaunch {
   int na, a_blk, nb, bx, by;
 };
 
+// B-side blocks cover 8 sub-steps x 16 columns (bx x by per source), from
+// row-major X or, with GATHER, from the convolution data.
 template <bool GATHER>
 __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ PlanesLaunch pl) {
-  __shared__ uint32_t tile[PB_WORDS];
-  __shared__ int tap_off[PB_TK], tap_r[PB_TK], tap_s[PB_TK];
   const i64 b = blockIdx.x;
   const i64 a_blocks = (i64)pl.na * pl.a_blk;
   if (b < a_blocks) {
@@ -1304,10 +1214,10 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
   const int r = (int)(b - a_blocks);
   const int bx = r % pl.bx, by = (r / pl.bx) % pl.by, z = r / (pl.bx * pl.by);
   if (GATHER)
-    planes_b_conv_tile(tile, tap_off, tap_r, tap_s, pl.cg, pl.jb, (int)pl.N, (int)pl.K,
-                       (int)pl.Kp, bx, by, z);
+    planes_b_conv_kmajor(pl.cg, pl.jb, (int)pl.N, (int)pl.K, (int)pl.Kp, bx, by, z);
   else
-    planes_b_tile(tile, DirectSrc{pl.jb.j[z].X1}, pl.jb.j[z].out, pl.N, pl.K, pl.Kp, bx, by);
+    planes_b_kmajor(DirectSrc{pl.jb.j[z].X1}, nullptr, pl.jb.j[z].out, nullptr, pl.N, pl.K, pl.Kp,
+                    bx, by);
 }
 
 // The digit planes of many products in one launch: a task is one operand
@@ -1334,7 +1244,6 @@ struct __align__(16) PlaneTask {
 
 __global__ void __launch_bounds__(256) limb_planes_grouped(const PlaneTask* __restrict__ tasks,
                                                            int ntasks) {
-  __shared__ uint32_t tile[PB_WORDS];
   const i64 b = blockIdx.x;
   int lo = 0, hi = ntasks - 1;
   while (lo < hi) {
@@ -1343,21 +1252,19 @@ __global__ void __launch_bounds__(256) limb_planes_grouped(const PlaneTask* __re
   }
   const PlaneTask& t = tasks[lo];
   const i64 local = b - t.block_base;
+  const int bx = (int)(local % t.bx), by = (int)(local / t.bx);
   if (t.nparty == 0) {
     const DirectSrc src{t.src};
     if (t.side == 0)
       planes_a_part(src, t.out, t.rows, t.K, t.Kp, local, t.nblk);
     else
-      planes_b_tile(tile, src, t.out, t.rows, t.K, t.Kp, (int)(local % t.bx), (int)(local / t.bx));
+      planes_b_kmajor(src, nullptr, t.out, nullptr, t.rows, t.K, t.Kp, bx, by);
   } else {
     const OpenedSrc src{t.src, t.sub, t.add, t.pstride, t.nparty};
     if (t.side == 0)
       planes_a_part(src, t.out, t.rows, t.K, t.Kp, local, t.nblk);
-    else if (t.out2)
-      planes_b_tile2(tile, src, t.add2, t.out, t.out2, t.rows, t.K, t.Kp, (int)(local % t.bx),
-                     (int)(local / t.bx));
     else
-      planes_b_tile(tile, src, t.out, t.rows, t.K, t.Kp, (int)(local % t.bx), (int)(local / t.bx));
+      planes_b_kmajor(src, t.add2, t.out, t.out2, t.rows, t.K, t.Kp, bx, by);
   }
 }
 
@@ -1466,7 +1373,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     return fail(MPC_ENOMEM, "limb workspace %zu bytes, need %zu", ws_bytes, need);
   const i64 gy = ceil_div(g.M, BM), gx = ceil_div(g.N, BN);
   if (gy > 65535) return fail(MPC_EUNSUPPORTED, "M too large for the limb engine grid");
-  if (ceil_div(g.N, PB_TN) > 65535) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
+  if (ceil_div(g.N, 16) > 0x7FFFFFFFll) return fail(MPC_EUNSUPPORTED, "N too large for the plane pass");
   int* st = device_status_ptr();
   if (!st) return fail(MPC_ECUDA, "device status word unavailable");
 
@@ -1536,8 +1443,8 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     pl.Kp = K1p;
     pl.na = na;
     pl.nb = nb;
-    pl.bx = (int)ceil_div(K1p, PB_TK);
-    pl.by = (int)ceil_div(g.N, PB_TN);
+    pl.bx = (int)ceil_div(K1p / KS, 8);  // B side: blocks of 8 sub-steps x 16 columns
+    pl.by = (int)ceil_div(g.N, 16);
     // A side: about as many threads as 8-k groups, at most 4 blocks per SM and job.
     pl.a_blk = (int)std::min<i64>(ceil_div(g.M * (K1p / 8), 256), 148 * 4);
     const i64 blocks = (i64)na * pl.a_blk + (i64)nb * pl.bx * pl.by;
@@ -1697,9 +1604,9 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
       t.side = aside ? 0 : 1;
       if (aside) {
         t.nblk = (int)std::min<i64>(ceil_div(g.M * (K1p / 8), 256), 148 * 4);
-      } else {
-        t.bx = (int)ceil_div(K1p, PB_TK);
-        t.nblk = t.bx * (int)ceil_div(g.N, PB_TN);
+      } else {  // blocks of 8 sub-steps x 16 columns
+        t.bx = (int)ceil_div(K1p / KS, 8);
+        t.nblk = t.bx * (int)ceil_div(g.N, 16);
       }
       block_base += t.nblk;
       ht.push_back(t);
