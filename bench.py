@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sizes", default="1024,2048,4096,8192")
     ap.add_argument("--elem-log2", default="20,22,24,26",
                     help="elementwise workload: log2 of the element counts")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="batched workload: number of products (the first of the seed-2 draw)")
     return ap.parse_args()
 
 
@@ -709,7 +711,8 @@ def run_batched(args):
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    print(json.dumps(measure_batched(dev, max(3, min(args.steps, 10)))), flush=True)
+    print(json.dumps(measure_batched(dev, max(3, min(args.steps, 10)), args.batch_count)),
+          flush=True)
 
 
 def extra_batched(dev, reps=3):
@@ -717,7 +720,7 @@ def extra_batched(dev, reps=3):
     return r
 
 
-def measure_batched(dev, reps):
+def measure_batched(dev, reps, count=512):
     """512 two-party Beaver matmuls with (M, N, K) log-uniform in [32, 2048] (seed 2).
 
     Times the online step (opening + products + truncation; triples dealt
@@ -730,7 +733,7 @@ def measure_batched(dev, reps):
     import paper_2109_00984_b300 as mpc
 
     P = 2
-    dims = synth.batched_dims()
+    dims = synth.batched_dims()[:count]
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     prods = []
@@ -809,8 +812,9 @@ def measure_batched(dev, reps):
     g.replay()
     t_graph = timed(g.replay, reps)
 
-    line = {"workload": "512 uneven 2-party Beaver matmuls, (M,N,K) log-uniform in [32,2048] "
-                        "(seed 2), truncation 2^16, online step (triples dealt beforehand)",
+    line = {"workload": f"{count} uneven 2-party Beaver matmuls, (M,N,K) log-uniform in "
+                        "[32,2048] (seed 2), truncation 2^16, online step (triples dealt "
+                        "beforehand)",
             "ring_ops_per_batch": ring_ops,
             "per_product_ms": t_each, "batched_ms": t_batched, "graph_ms": t_graph,
             "per_product_ring_tops": ring_ops / (t_each / 1e3) / 1e12,
