@@ -76,10 +76,16 @@ __global__ void __launch_bounds__(kThreads) fill_sum_kernel(int P, i64 n, u64 se
   }
 }
 
-// Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1; C[P-1] holds c on
-// entry and becomes c - sum_{p<P-1} C[p].
+// Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1 and C[P-1] =
+// c - sum_{p<P-1} C[p].  c is C[P-1] on entry, or, when the product's GEMM was
+// split along K (part != null), the sum of its `splits` partial sums
+// part[s][M][N] at the GEMM position of each output index (the NCHW scatter
+// of gemm_out_index when hw_out != 0): the reduction kernel is folded in.
 __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u64 seed,
-                                                                 u64 op_id, u64* __restrict__ C) {
+                                                                 u64 op_id, u64* __restrict__ C,
+                                                                 const u64* __restrict__ part,
+                                                                 int splits, i64 M, i64 N,
+                                                                 i64 hw_out) {
   const i64 nblk = ceil_div(n, 4);
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
        t += (i64)gridDim.x * blockDim.x) {
@@ -94,9 +100,40 @@ __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (i0 + j < n) C[(i64)(P - 1) * n + i0 + j] -= acc[j];
+    for (int j = 0; j < 4; ++j) {
+      const i64 i = i0 + j;
+      if (i >= n) continue;
+      u64 c;
+      if (part) {
+        i64 row, col;
+        if (hw_out) {  // i = (b M + row) hw + pos, col = b hw + pos
+          const i64 q = i / hw_out, pos = i - q * hw_out;
+          const i64 b = q / M;
+          row = q - b * M;
+          col = b * hw_out + pos;
+        } else {
+          row = i / N;
+          col = i - row * N;
+        }
+        c = 0;
+        for (int sp = 0; sp < splits; ++sp) c += part[(i64)sp * M * N + row * N + col];
+      } else {
+        c = C[(i64)(P - 1) * n + i];
+      }
+      C[(i64)(P - 1) * n + i] = c - acc[j];
+    }
   }
+}
+
+// The dealer's product c of a one-job GEMM set (as launched, splits deferred)
+// shared out as C.
+int share_product(int P, const GemmArgs& used, u64 seed, u64 op_id, u64* C, cudaStream_t s) {
+  const i64 n = used.M * used.N;
+  const bool split = used.splits > 1;
+  share_product_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(
+      P, n, seed, op_id, C, split ? used.partial : nullptr, split ? used.splits : 1, used.M,
+      used.N, used.hw_out);
+  return check_launch("share product");
 }
 
 // im2col over the ring: col[k][c] with k = (ci * kh + r) * kw + s and
@@ -510,10 +547,10 @@ int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed,
   g.K = K;
   g.njobs = 1;
   g.jobs[0] = GemmJob{a, b, nullptr, nullptr, nullptr, Clast};
-  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s)) return rc;
-  share_product_kernel<<<grid_for(ceil_div(M * N, 4), kThreads), kThreads, 0, s>>>(
-      P, M * N, seed, op_id, (u64*)C);
-  return check_launch("share product");
+  g.defer_reduce = 1;  // the correction kernel adds the split-K partial sums itself
+  GemmArgs used{};
+  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, &used)) return rc;
+  return share_product(P, used, seed, op_id, (u64*)C, s);
 }
 
 size_t mpc_conv2d_triple_workspace_size(int P, const mpc_conv_desc* d, int algo) {
@@ -570,10 +607,10 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   g.njobs = 1;
   g.gather = gather ? &cg : nullptr;
   g.jobs[0] = GemmJob{b, acol, nullptr, nullptr, nullptr, Clast};
-  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s)) return rc;
-  share_product_kernel<<<grid_for(ceil_div(M * N, 4), kThreads), kThreads, 0, s>>>(
-      P, M * N, seed, op_id, (u64*)C);
-  return check_launch("share product");
+  g.defer_reduce = 1;  // the correction kernel adds the split-K partial sums itself
+  GemmArgs used{};
+  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, &used)) return rc;
+  return share_product(P, used, seed, op_id, (u64*)C, s);
 }
 
 }  // extern "C"
