@@ -52,13 +52,13 @@ def _to_dev(prods, P):
     return out
 
 
-@pytest.mark.parametrize("P", [2, 3])
+@pytest.mark.parametrize("P", [1, 2, 3, 8])
 @pytest.mark.parametrize("mode", ["plain", "limb", "mixed", "limb_3ctas", "limb_1cta"])
 def test_batched_matches_oracle(mpc, P, mode, rng):
     """limb_3ctas / limb_1cta: the persistent limb kernel on 3 CTAs or 1, so
     each CTA runs many tiles of products of different K back to back (the
     barrier phases, chunk counts and TMEM slots carry over between tiles)."""
-    dims, prods, refs = _small_batch(rng, P, 17)
+    dims, prods, refs = _small_batch(rng, P, 17, hi=300 if P < 8 else 140)
     dprods = _to_dev(prods, P)
     tune = mpc.default_tune()
     if mode == "mixed":
