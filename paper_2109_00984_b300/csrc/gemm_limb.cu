@@ -41,17 +41,21 @@
 // K-concatenated operand pairs (Z = C + A1 B1 + A2 B2) are one GEMM over
 // [A1 | A2] and [B1 ; B2], each pair with its own planes.
 //
-// Warp roles (640 threads): warps 0-3 each issue the MMAs of one accumulator
-// slot q (shift q in pass 0, 4 + q in pass 1), one thread per warp; that
-// thread of warp 0 also issues the TMA loads, STAGES - 1 sub-steps ahead of
-// its own MMAs; warp 0 allocates TMEM; warps 4-19 drain TMEM, four per lane
-// quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each, and write
-// the output.  After launch (96 registers per thread) the issuing warpgroup
-// drops to 56 and the drain warpgroups rise to 104 (setmaxnreg), so a drain
-// can hold a slot's 32 loaded columns beside its 32 64-bit sums and release
-// the slot before converting.  Every wait is bounded: on a timeout the CTA records
-// MPC_ETIMEOUT, waits (bounded) for its own copies and MMAs, frees TMEM and
-// returns.
+// Warp roles of the one-launch kernel (768 threads): warps 0-3 each issue the
+// MMAs of one accumulator slot q (shift q in pass 0, 4 + q in pass 1), one
+// thread per warp; one thread of warp 4 issues every TMA load, as soon as a
+// stage is released (an MMA issue holds its thread until the tensor pipe takes
+// it, so a loader that also issued MMAs delivered its stages late); warps 5-7
+// complete that warpgroup; warp 0 allocates TMEM; warps 8-23 drain TMEM, four
+// per lane quadrant (warp w reads lanes 32 (w % 4) .. +31), 32 columns each,
+// and write the output.  A pass-0 stage holds two sub-steps (planes 0..3 of t
+// and of t + 1), so each barrier round trip of pass 0 feeds 20 MMAs.  After
+// launch (80 registers per thread) the MMA warpgroup drops to 40, the producer
+// warpgroup to 24 and the drain warpgroups rise to 104 (setmaxnreg), so a
+// drain can hold a slot's 32 loaded columns beside its 32 64-bit sums and
+// release the slot before converting.  Every wait is bounded: on a timeout the
+// CTA records MPC_ETIMEOUT, waits (bounded) for its own copies and MMAs, frees
+// TMEM and returns.
 //
 // A persistent variant (limb_gemm_grouped_kernel) runs the tiles of a whole
 // batch of Beaver matmuls: one CTA per SM claims 128 x 128 tiles of any
@@ -81,8 +85,8 @@ constexpr int A_STAGE_BYTES = NPLANE * PLANE_BYTES;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_STAGE_BYTES;         // A then B planes: 64 KiB
 constexpr int HALF_LOAD_BYTES = 4 * PLANE_BYTES;       // one TMA box: 128 rows x 128 B
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int kIssuers = 4;      // MMA-issuing warps (0..3); warp 0 also loads
-constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps (4..19)
+constexpr int kIssuers = 4;      // MMA-issuing warps (0..3); in the grouped kernel warp 0 also loads
+constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps
 // 20 warps, 5 per SM sub-partition: up to 96 registers per thread (the drain
 // warps hold 32 64-bit sums each).
 constexpr int kThreads = 32 * (kIssuers + kDrainWarps);
@@ -93,6 +97,21 @@ constexpr int kLaunchRegs = 96, kIssuerRegs = 56, kDrainRegs = 104;
 static_assert(kIssuers == 4 && kDrainWarps % 4 == 0, "warpgroup-aligned roles");
 static_assert(32 * kIssuers * kIssuerRegs + 32 * kDrainWarps * kDrainRegs <= kThreads * kLaunchRegs,
               "register split exceeds the launch allocation");
+// The one-launch kernel (limb_gemm_kernel) runs 24 warps: warps 0-3 issue the
+// MMAs of accumulator slots 0-3, warp 4 issues the TMA loads, warps 5-7 only
+// complete that warpgroup, warps 8-23 drain.  A tcgen05.mma holds its thread
+// until the tensor pipe takes it (about 120 cycles for one thread alone, 200+
+// with four competing), so a loader that also issues MMAs delivers each stage
+// late; on its own warp it refills a stage as soon as the MMAs release it.
+// Launched with 80 registers per thread (768 threads); after launch the MMA
+// warpgroup keeps 40, the producer warpgroup 24, the drain warpgroups take 104.
+constexpr int kOneWarps = 24, kOneThreads = 32 * kOneWarps, kOneDrainBase = 8;
+constexpr int kOneLaunchRegs = 80, kOneIssuerRegs = 40, kOneProducerRegs = 24;
+static_assert(32 * 4 * kOneIssuerRegs + 32 * 4 * kOneProducerRegs + 32 * kDrainWarps * kDrainRegs <=
+                  kOneThreads * kOneLaunchRegs,
+              "register split exceeds the launch allocation");
+static_assert(kOneDrainBase % 4 == 0 && kOneDrainBase + kDrainWarps == kOneWarps,
+              "drain warps fill whole warpgroups");
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(BM == BN, "A and B plane tiles share one layout");
 static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "epilogue tile fits the stages");
@@ -257,103 +276,149 @@ __device__ __forceinline__ int chunk_left(int t, int s) {
   return L - (t + (s & 3) * L / 4) % L;
 }
 
-// TMA loads of sub-step g (over both passes): pass 0 digit planes 0..3 of A and
-// B, pass 1 all eight.  Waits (bounded) until every issuer released the stage.
-struct Loader {
-  const LimbParams* p;
-  uint32_t sbase;
-  int job, m0, n0, t_begin, steps;
-  uint64_t *full_bar, *empty_bar;
-  volatile int* abort_flag;
-  int last_g[STAGES];
-  __device__ __forceinline__ bool load(int g) {
-    const int pass = g >= steps;
-    const int t = t_begin + g - pass * steps;
-    const int pair = t >= p->T1;
-    const int tl = t - pair * p->T1;
-    const CUtensorMap* ta = &p->tmA[pair][job];
-    const CUtensorMap* tb = &p->tmB[pair][job];
-    const int st = g % STAGES;
-    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-    if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) return false;
-    mbar_arrive_expect_tx(&full_bar[st], (pass ? 4 : 2) * HALF_LOAD_BYTES);
-    const uint32_t a_dst = sbase + st * STAGE_BYTES;
-    const uint32_t b_dst = a_dst + A_STAGE_BYTES;
-    tma_load_4d(a_dst, ta, &full_bar[st], 0, 0, tl, m0);
-    tma_load_4d(b_dst, tb, &full_bar[st], 0, 0, tl, n0);
-    if (pass) {
-      tma_load_4d(a_dst + HALF_LOAD_BYTES, ta, &full_bar[st], 0, 1, tl, m0);
-      tma_load_4d(b_dst + HALF_LOAD_BYTES, tb, &full_bar[st], 0, 1, tl, n0);
-    }
-    last_g[st] = g;
-    return true;
-  }
-  // Copies in flight must land before the CTA can leave (bounded).
-  __device__ __forceinline__ void drain_copies() {
-    for (int i = 0; i < STAGES; ++i) {
-      if (last_g[i] < 0) continue;
-      const uint32_t ph = (uint32_t)(last_g[i] / STAGES) & 1u;
-      const unsigned long long t0 = globaltimer();
-      while (!mbar_try_wait(&full_bar[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
-      }
-    }
-  }
-};
+// Descriptor offset between consecutive stages (16-byte units).
+constexpr uint64_t STAGE_DESC = STAGE_BYTES >> 4;
 
-// MMA issuer of accumulator slot q: shift q in pass 0, 4 + q in pass 1.  g
-// counts sub-steps over both passes (pipeline stage and phase); a chunk starts
-// at the range's first sub-step or right after the previous one ended, and
-// waits until the drain warps have read the slot's previous chunk (which may
-// belong to pass 0).  With a Loader (slot 0) the thread also keeps the TMA
-// loads STAGES - 1 sub-steps ahead: the load of g + STAGES - 1 reuses the
-// stage of g - 1, which this thread has already released.
-__device__ __forceinline__ void issuer_loop(int q, uint32_t sbase, uint32_t tmem, int t_begin,
-                                            int t_end, uint64_t* full_bar, uint64_t* empty_bar,
-                                            uint64_t* accf_bar, uint64_t* acce_bar,
-                                            volatile int* abort_flag, Loader* ld) {
-  const int steps = t_end - t_begin, total = 2 * steps;
-  int gl = 0;
-  if (ld)
-    for (; gl < STAGES - 1 && gl < total; ++gl)
-      if (!ld->load(gl)) return;
-  uint32_t chunks = 0;
-  const uint32_t d = tmem + (uint32_t)(q * BN);
-  int left = 0;
-  bool start = true;
-  for (int g = 0; g < total; ++g) {
-    if (ld && gl < total) {
-      if (!ld->load(gl)) return;
-      ++gl;
+// Copies in flight must land before the CTA can leave (bounded): the last
+// load into each stage, out of the n issued.
+__device__ __forceinline__ void drain_copies(int n, uint64_t* full_bar) {
+  for (int i = 0; i < STAGES && i < n; ++i) {
+    const int last = n - 1 - ((n - 1 - i) % STAGES);
+    const uint32_t ph = (uint32_t)(last / STAGES) & 1u;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(&full_bar[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
     }
-    const int pass = g >= steps;
-    const int t = t_begin + g - pass * steps;
-    const int shift = 4 * pass + q;
-    if (t == t_begin) {
-      left = chunk_left(t, shift);
-      start = true;
-    }
-    const int st = g % STAGES;
-    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-    if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
-    tc_fence_after();
-    const uint64_t a0 = smem_desc_sw128(sbase + st * STAGE_BYTES);
-    const uint64_t b0 = smem_desc_sw128(sbase + st * STAGE_BYTES + A_STAGE_BYTES);
-    if (start && chunks > 0) {
-      if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return;
-      tc_fence_after();
-    }
-    issue_shift(d, a0, b0, shift, start);
-    start = --left == 0 || t == t_end - 1;
-    if (start) {
-      tc_commit(&accf_bar[q]);
-      chunks++;
-      left = chunk_len(shift);
-    }
-    tc_commit(&empty_bar[st]);
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
+// The producer (warp 4, one thread): every load of the CTA's sub-steps in
+// order, each as soon as its stage is released, so STAGES stages are in
+// flight.  A pass-0 stage carries two sub-steps (digit planes 0..3 of t where
+// a pass-1 stage keeps planes 0..3, those of t + 1 where it keeps 4..7), so
+// every barrier round trip of pass 0 feeds 20 MMAs instead of 10.
+__device__ __forceinline__ void producer_loop(const LimbParams& p, int job, int m0, int n0,
+                                              uint32_t sbase, int t_begin, int t_end,
+                                              uint64_t* full_bar, uint64_t* empty_bar,
+                                              volatile int* abort_flag) {
+  const CUtensorMap* ta[2] = {&p.tmA[0][job], &p.tmA[1][job]};
+  const CUtensorMap* tb[2] = {&p.tmB[0][job], &p.tmB[1][job]};
+  const int T1 = p.T1;
+  int st = 0, n = 0;
+  uint32_t ph = 0;
+  // One box of digit planes (plane group h: 0..3 or 4..7) of sub-step t of A
+  // and of B, into the two halves at offset `half` of the stage.
+  auto box = [&](int t, int h, uint32_t half) {
+    const int pair = t >= T1;
+    const int tl = pair ? t - T1 : t;
+    const uint32_t a_dst = sbase + (uint32_t)st * STAGE_BYTES + half;
+    tma_load_4d(a_dst, pair ? ta[1] : ta[0], &full_bar[st], 0, h, tl, m0);
+    tma_load_4d(a_dst + A_STAGE_BYTES, pair ? tb[1] : tb[0], &full_bar[st], 0, h, tl, n0);
+  };
+  auto next = [&]() {
+    ++n;
+    if (++st == STAGES) {
+      st = 0;
+      ph ^= 1u;
+    }
+  };
+  bool ok = true;
+  for (int t = t_begin; t < t_end && ok; t += 2) {
+    const bool two = t + 1 < t_end;
+    if (!(ok = mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag))) break;
+    mbar_arrive_expect_tx(&full_bar[st], (two ? 4 : 2) * HALF_LOAD_BYTES);
+    box(t, 0, 0);
+    if (two) box(t + 1, 0, HALF_LOAD_BYTES);
+    next();
+  }
+  for (int t = t_begin; t < t_end && ok; ++t) {
+    if (!(ok = mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag))) break;
+    mbar_arrive_expect_tx(&full_bar[st], 4 * HALF_LOAD_BYTES);
+    box(t, 0, 0);
+    box(t, 1, HALF_LOAD_BYTES);
+    next();
+  }
+  drain_copies(n, full_bar);
+}
+
+// One accumulator slot's MMA schedule: shift q in pass 0, 4 + q in pass 1; a
+// chunk starts at the range's first sub-step or right after the previous one
+// ended, and first waits until the drain warps have read the slot's previous
+// chunk (which may belong to pass 0).
+struct Slot {
+  uint32_t d;       // TMEM address of the accumulator
+  int q, shift, len, left;
+  bool start;
+  uint32_t chunks;  // chunks committed so far
+  __device__ __forceinline__ void begin_pass(int pass, int t_begin, uint32_t tmem) {
+    d = tmem + (uint32_t)(q * BN);
+    shift = 4 * pass + q;
+    len = chunk_len(shift);
+    left = chunk_left(t_begin, shift);
+    start = true;
+  }
+  // The slot's MMAs of one sub-step; false on an abort.
+  __device__ __forceinline__ bool step(uint64_t a0, uint64_t b0, bool last, uint64_t* accf_bar,
+                                       uint64_t* acce_bar, volatile int* abort_flag) {
+    if (start && chunks > 0) {
+      if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return false;
+      tc_fence_after();
+    }
+    issue_shift(d, a0, b0, shift, start);
+    start = --left == 0 || last;
+    if (start) {
+      tc_commit(&accf_bar[q]);
+      chunks++;
+      left = len;
+    }
+    return true;
+  }
+};
+
+// MMA issuer of accumulator slot q (warp q): pass 0 two sub-steps per stage
+// (the second one's planes 0..3 where pass 1 keeps planes 4..7), pass 1 one;
+// the stage and its phase are kept as counters.
+__device__ __forceinline__ void mma_loop(int q, uint32_t sbase, uint32_t tmem, int t_begin,
+                                         int t_end, uint64_t* full_bar, uint64_t* empty_bar,
+                                         uint64_t* accf_bar, uint64_t* acce_bar,
+                                         volatile int* abort_flag) {
+  Slot sl{0, q, 0, 0, 0, true, 0u};
+  const uint64_t a_base = smem_desc_sw128(sbase);
+  const uint64_t b_base = smem_desc_sw128(sbase + A_STAGE_BYTES);
+  constexpr uint64_t HALF_DESC = HALF_LOAD_BYTES >> 4;
+  int st = 0;
+  uint32_t ph = 0;
+  auto next = [&]() {
+    if (++st == STAGES) {
+      st = 0;
+      ph ^= 1u;
+    }
+  };
+  sl.begin_pass(0, t_begin, tmem);
+  for (int t = t_begin; t < t_end; t += 2) {
+    if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
+    tc_fence_after();
+    const uint64_t a0 = a_base + (uint64_t)st * STAGE_DESC;
+    const uint64_t b0 = b_base + (uint64_t)st * STAGE_DESC;
+    if (!sl.step(a0, b0, t == t_end - 1, accf_bar, acce_bar, abort_flag)) return;
+    if (t + 1 < t_end &&
+        !sl.step(a0 + HALF_DESC, b0 + HALF_DESC, t + 1 == t_end - 1, accf_bar, acce_bar, abort_flag))
+      return;
+    tc_commit(&empty_bar[st]);
+    next();
+  }
+  sl.begin_pass(1, t_begin, tmem);
+  for (int t = t_begin; t < t_end; ++t) {
+    if (!mbar_wait(&full_bar[st], ph, abort_flag)) return;
+    tc_fence_after();
+    const uint64_t a0 = a_base + (uint64_t)st * STAGE_DESC;
+    const uint64_t b0 = b_base + (uint64_t)st * STAGE_DESC;
+    if (!sl.step(a0, b0, t == t_end - 1, accf_bar, acce_bar, abort_flag)) return;
+    tc_commit(&empty_bar[st]);
+    next();
+  }
+}
+
+__global__ void __launch_bounds__(kOneThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
   __shared__ __align__(8) uint64_t accf_bar[NSLOT], acce_bar[NSLOT], done_bar;
@@ -400,36 +465,28 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   const int steps = t_end - t_begin;
 
   if (warp < kIssuers) {
-    // The issuing warpgroup hands registers to the drain warpgroups:
-    // 128 x 56 + 512 x 104 = 60 416 <= 640 x 96 launched.
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssuerRegs));
+    // The MMA and producer warpgroups hand registers to the drain warpgroups:
+    // 128 x 40 + 128 x 24 + 512 x 104 = 61 440 = 768 x 80 launched.
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kOneIssuerRegs));
     if (lane == 0) {
-      // ---- MMA issuers: warp q owns accumulator slot q; warp 0 also loads ----
-      Loader ldr;
-      ldr.p = &p;
-      ldr.sbase = sbase;
-      ldr.job = job;
-      ldr.m0 = m0;
-      ldr.n0 = n0;
-      ldr.t_begin = t_begin;
-      ldr.steps = steps;
-      ldr.full_bar = full_bar;
-      ldr.empty_bar = empty_bar;
-      ldr.abort_flag = &abort_flag;
-      for (int i = 0; i < STAGES; ++i) ldr.last_g[i] = -1;
-      issuer_loop(warp, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar, acce_bar,
-                  &abort_flag, warp == 0 ? &ldr : nullptr);
-      if (warp == 0) ldr.drain_copies();
+      // ---- MMA issuers: warp q owns accumulator slot q ----
+      mma_loop(warp, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar, acce_bar,
+               &abort_flag);
       // All of this issuer's MMAs must finish before TMEM is released (bounded).
       tc_commit(&done_bar);
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(&done_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
       }
     }
+  } else if (warp < kOneDrainBase) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kOneProducerRegs));
+    // ---- the producer: TMA loads only ----
+    if (warp == kIssuers && lane == 0)
+      producer_loop(p, job, m0, n0, sbase, t_begin, t_end, full_bar, empty_bar, &abort_flag);
   } else {
     // ---- TMEM drain + epilogue: 16 warps, four per TMEM lane quadrant ----
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs));
-    const int ew = warp - kIssuers;               // 0..15
+    const int ew = warp - kOneDrainBase;          // 0..15
     const int quad = warp & 3;                    // lane quadrant this warp may access
     const int cblk = ew >> 2;                     // which 32 of the 128 columns
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cblk * 32);
@@ -1478,7 +1535,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(g.njobs * g.splits));
   {
     KernelTimer timer("gemm_limb", s);
-    limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
+    limb_gemm_kernel<<<grid, kOneThreads, SMEM_BYTES, s>>>(prm);
     if (int rc = check_launch("gemm_limb")) return rc;
   }
   return (g.splits > 1 && !g.defer_reduce) ? gemm_reduce(g, s) : MPC_OK;
