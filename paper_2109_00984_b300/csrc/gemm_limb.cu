@@ -85,33 +85,26 @@ constexpr int A_STAGE_BYTES = NPLANE * PLANE_BYTES;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_STAGE_BYTES;         // A then B planes: 64 KiB
 constexpr int HALF_LOAD_BYTES = 4 * PLANE_BYTES;       // one TMA box: 128 rows x 128 B
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int kIssuers = 4;      // MMA-issuing warps (0..3); in the grouped kernel warp 0 also loads
-constexpr int kDrainWarps = 16;  // TMEM drain / epilogue warps
-// 20 warps, 5 per SM sub-partition: up to 96 registers per thread (the drain
-// warps hold 32 64-bit sums each).
-constexpr int kThreads = 32 * (kIssuers + kDrainWarps);
-// Register split after launch (setmaxnreg): the issuing warpgroup keeps 56 per
-// thread, the drain warpgroups take 104, enough to hold a slot's 32 drained
-// columns beside the 32 64-bit sums.
-constexpr int kLaunchRegs = 96, kIssuerRegs = 56, kDrainRegs = 104;
-static_assert(kIssuers == 4 && kDrainWarps % 4 == 0, "warpgroup-aligned roles");
-static_assert(32 * kIssuers * kIssuerRegs + 32 * kDrainWarps * kDrainRegs <= kThreads * kLaunchRegs,
+// Warp roles (both kernels, 24 warps): warps 0-3 issue the MMAs of
+// accumulator slots 0-3, warp 4 issues the TMA loads, warps 5-7 only complete
+// that warpgroup, warps 8-23 drain.  A tcgen05.mma holds its thread until the
+// tensor pipe takes it (about 120 cycles for one thread alone, 200+ with four
+// competing), so a loader that also issued MMAs delivered each stage late; on
+// its own warp it refills a stage as soon as the MMAs release it.
+constexpr int kIssuers = 4;        // MMA-issuing warps 0..3, one accumulator slot each
+constexpr int kProducerWarp = 4;   // TMA loads (one thread)
+constexpr int kDrainBase = 8;      // first TMEM drain / epilogue warp
+constexpr int kDrainWarps = 16;
+constexpr int kWarps = kDrainBase + kDrainWarps, kThreads = 32 * kWarps;
+// Launched with 80 registers per thread (768 threads); after launch
+// (setmaxnreg) the MMA warpgroup keeps 40, the producer warpgroup 24 and the
+// drain warpgroups take 104, enough to hold a slot's 32 drained columns beside
+// the 32 64-bit sums.
+constexpr int kLaunchRegs = 80, kIssuerRegs = 40, kProducerRegs = 24, kDrainRegs = 104;
+static_assert(kIssuers == 4 && kDrainBase % 4 == 0 && kDrainWarps % 4 == 0, "warpgroup-aligned roles");
+static_assert(32 * 4 * kIssuerRegs + 32 * 4 * kProducerRegs + 32 * kDrainWarps * kDrainRegs <=
+                  kThreads * kLaunchRegs,
               "register split exceeds the launch allocation");
-// The one-launch kernel (limb_gemm_kernel) runs 24 warps: warps 0-3 issue the
-// MMAs of accumulator slots 0-3, warp 4 issues the TMA loads, warps 5-7 only
-// complete that warpgroup, warps 8-23 drain.  A tcgen05.mma holds its thread
-// until the tensor pipe takes it (about 120 cycles for one thread alone, 200+
-// with four competing), so a loader that also issues MMAs delivers each stage
-// late; on its own warp it refills a stage as soon as the MMAs release it.
-// Launched with 80 registers per thread (768 threads); after launch the MMA
-// warpgroup keeps 40, the producer warpgroup 24, the drain warpgroups take 104.
-constexpr int kOneWarps = 24, kOneThreads = 32 * kOneWarps, kOneDrainBase = 8;
-constexpr int kOneLaunchRegs = 80, kOneIssuerRegs = 40, kOneProducerRegs = 24;
-static_assert(32 * 4 * kOneIssuerRegs + 32 * 4 * kOneProducerRegs + 32 * kDrainWarps * kDrainRegs <=
-                  kOneThreads * kOneLaunchRegs,
-              "register split exceeds the launch allocation");
-static_assert(kOneDrainBase % 4 == 0 && kOneDrainBase + kDrainWarps == kOneWarps,
-              "drain warps fill whole warpgroups");
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(BM == BN, "A and B plane tiles share one layout");
 static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "epilogue tile fits the stages");
@@ -418,7 +411,7 @@ __device__ __forceinline__ void mma_loop(int q, uint32_t sbase, uint32_t tmem, i
   }
 }
 
-__global__ void __launch_bounds__(kOneThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
+__global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_constant__ LimbParams p) {
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
   __shared__ __align__(8) uint64_t accf_bar[NSLOT], acce_bar[NSLOT], done_bar;
@@ -467,7 +460,7 @@ __global__ void __launch_bounds__(kOneThreads, 1) limb_gemm_kernel(const __grid_
   if (warp < kIssuers) {
     // The MMA and producer warpgroups hand registers to the drain warpgroups:
     // 128 x 40 + 128 x 24 + 512 x 104 = 61 440 = 768 x 80 launched.
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kOneIssuerRegs));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssuerRegs));
     if (lane == 0) {
       // ---- MMA issuers: warp q owns accumulator slot q ----
       mma_loop(warp, sbase, tmem, t_begin, t_end, full_bar, empty_bar, accf_bar, acce_bar,
@@ -478,15 +471,15 @@ __global__ void __launch_bounds__(kOneThreads, 1) limb_gemm_kernel(const __grid_
       while (!mbar_try_wait(&done_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
       }
     }
-  } else if (warp < kOneDrainBase) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kOneProducerRegs));
+  } else if (warp < kDrainBase) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
     // ---- the producer: TMA loads only ----
-    if (warp == kIssuers && lane == 0)
+    if (warp == kProducerWarp && lane == 0)
       producer_loop(p, job, m0, n0, sbase, t_begin, t_end, full_bar, empty_bar, &abort_flag);
   } else {
     // ---- TMEM drain + epilogue: 16 warps, four per TMEM lane quadrant ----
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs));
-    const int ew = warp - kOneDrainBase;          // 0..15
+    const int ew = warp - kDrainBase;          // 0..15
     const int quad = warp & 3;                    // lane quadrant this warp may access
     const int cblk = ew >> 2;                     // which 32 of the 128 columns
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cblk * 32);
@@ -649,116 +642,86 @@ __shared__ long long gq_item[2];
 // Stage buffers: 1024-byte aligned start of the dynamic shared memory.
 __device__ __forceinline__ uint32_t stage_base() { return (smem_u32(gq_smem) + 1023u) & ~1023u; }
 
-// TMA loads of sub-step g of a tile (over both passes): pass 0 digit planes
-// 0..3 of A and B, pass 1 all eight.  Waits (bounded) until every issuer
-// released the stage.  G0 is the CTA-wide number of the tile's first sub-step.
-struct TileLoader {
-  // The tile's fields the loads need, copied at the tile's start (read from
-  // shared memory on every sub-step they would sit on the loading thread's
-  // critical path).
-  const CUtensorMap* ta[2];
-  const CUtensorMap* tb[2];
-  int m0, n0, T1, t_begin, steps;
-  uint32_t G0;
-  int last_g[STAGES];  // CTA-wide number of the last load into each stage (-1: none)
-  __device__ __forceinline__ void start_tile(const TileJob& jb, uint32_t g0) {
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {
-      ta[pr] = jb.ta[pr];
-      tb[pr] = jb.tb[pr];
-    }
-    m0 = jb.m0;
-    n0 = jb.n0;
-    T1 = jb.T1;
-    t_begin = jb.t_begin;
-    steps = jb.t_end - jb.t_begin;
-    G0 = g0;
-  }
-  __device__ __forceinline__ bool load(int g) {
-    const int pass = g >= steps;
-    const int t = t_begin + g - pass * steps;
+// The loads of one tile of the grouped launch (the producer thread), in the
+// order of the one-launch kernel: pass-0 stages of two sub-steps, pass-1
+// stages of one.  The stage, its phase and the count of stage uses run on
+// from tile to tile.  False on an abort.
+__device__ __forceinline__ bool producer_tile(const TileJob& jb, int& st, uint32_t& ph, int& n) {
+  const CUtensorMap* ta[2] = {jb.ta[0], jb.ta[1]};
+  const CUtensorMap* tb[2] = {jb.tb[0], jb.tb[1]};
+  const int m0 = jb.m0, n0 = jb.n0, T1 = jb.T1, t_begin = jb.t_begin, t_end = jb.t_end;
+  const uint32_t sbase = stage_base();
+  auto box = [&](int t, int h, uint32_t half) {
     const int pair = t >= T1;
-    const int tl = t - pair * T1;
-    const CUtensorMap* tma = ta[pair];
-    const CUtensorMap* tmb = tb[pair];
-    const uint32_t G = G0 + (uint32_t)g;
-    const int st = (int)(G % STAGES);
-    const uint32_t ph = (G / STAGES) & 1u;
+    const int tl = pair ? t - T1 : t;
+    const uint32_t a_dst = sbase + (uint32_t)st * STAGE_BYTES + half;
+    tma_load_4d(a_dst, pair ? ta[1] : ta[0], &gq_full[st], 0, h, tl, m0);
+    tma_load_4d(a_dst + A_STAGE_BYTES, pair ? tb[1] : tb[0], &gq_full[st], 0, h, tl, n0);
+  };
+  auto next = [&]() {
+    ++n;
+    if (++st == STAGES) {
+      st = 0;
+      ph ^= 1u;
+    }
+  };
+  for (int t = t_begin; t < t_end; t += 2) {
+    const bool two = t + 1 < t_end;
     if (!mbar_wait(&gq_empty[st], ph ^ 1u, &gq_abort)) return false;
-    mbar_arrive_expect_tx(&gq_full[st], (pass ? 4 : 2) * HALF_LOAD_BYTES);
-    const uint32_t a_dst = stage_base() + st * STAGE_BYTES;
-    const uint32_t b_dst = a_dst + A_STAGE_BYTES;
-    tma_load_4d(a_dst, tma, &gq_full[st], 0, 0, tl, m0);
-    tma_load_4d(b_dst, tmb, &gq_full[st], 0, 0, tl, n0);
-    if (pass) {
-      tma_load_4d(a_dst + HALF_LOAD_BYTES, tma, &gq_full[st], 0, 1, tl, m0);
-      tma_load_4d(b_dst + HALF_LOAD_BYTES, tmb, &gq_full[st], 0, 1, tl, n0);
-    }
-    last_g[st] = (int)G;
-    return true;
+    mbar_arrive_expect_tx(&gq_full[st], (two ? 4 : 2) * HALF_LOAD_BYTES);
+    box(t, 0, 0);
+    if (two) box(t + 1, 0, HALF_LOAD_BYTES);
+    next();
   }
-  // Copies in flight must land before the CTA can leave (bounded).
-  __device__ __forceinline__ void drain_copies() {
-    for (int i = 0; i < STAGES; ++i) {
-      if (last_g[i] < 0) continue;
-      const uint32_t ph = ((uint32_t)last_g[i] / STAGES) & 1u;
-      const unsigned long long t0 = globaltimer();
-      while (!mbar_try_wait(&gq_full[i], ph) && globaltimer() - t0 < kWaitLimitNs) {
-      }
-    }
+  for (int t = t_begin; t < t_end; ++t) {
+    if (!mbar_wait(&gq_empty[st], ph ^ 1u, &gq_abort)) return false;
+    mbar_arrive_expect_tx(&gq_full[st], 4 * HALF_LOAD_BYTES);
+    box(t, 0, 0);
+    box(t, 1, HALF_LOAD_BYTES);
+    next();
   }
-};
+  return true;
+}
 
-// MMA issuer of accumulator slot q for one tile: shift q in pass 0, 4 + q in
-// pass 1.  g counts the tile's sub-steps over both passes (G0 + g: pipeline
-// stage and phase); a chunk starts at the range's first sub-step or right
-// after the previous one ended, and waits until the drain warps have read the
-// slot's previous chunk (which may belong to pass 0, or to the previous tile).
-// With a TileLoader (slot 0) the thread also keeps the TMA loads STAGES - 1
-// sub-steps ahead: the load of g + STAGES - 1 reuses the stage of g - 1, which
-// this thread has already released.  Returns false on an abort.
-__device__ __forceinline__ bool issuer_tile(int q, uint32_t tmem, const TileJob& jb, uint32_t G0,
-                                            uint32_t& chunks, TileLoader* ld) {
+// The MMAs of one tile for accumulator slot sl.q (one thread of warp q), in
+// the producer's stage order; the slot's chunk count (for the drain barrier's
+// parity), the stage and its phase run on from tile to tile.  False on an
+// abort.
+__device__ __forceinline__ bool mma_tile(Slot& sl, uint32_t tmem, const TileJob& jb, int& st,
+                                         uint32_t& ph) {
   const int t_begin = jb.t_begin, t_end = jb.t_end;
-  const int steps = t_end - t_begin, total = 2 * steps;
-  int gl = 0;
-  if (ld)
-    for (; gl < STAGES - 1 && gl < total; ++gl)
-      if (!ld->load(gl)) return false;
-  const uint32_t d = tmem + (uint32_t)(q * BN);
-  int left = 0;
-  bool start = true;
-  for (int g = 0; g < total; ++g) {
-    if (ld && gl < total) {
-      if (!ld->load(gl)) return false;
-      ++gl;
+  const uint32_t sbase = stage_base();
+  const uint64_t a_base = smem_desc_sw128(sbase);
+  const uint64_t b_base = smem_desc_sw128(sbase + A_STAGE_BYTES);
+  constexpr uint64_t HALF_DESC = HALF_LOAD_BYTES >> 4;
+  auto next = [&]() {
+    if (++st == STAGES) {
+      st = 0;
+      ph ^= 1u;
     }
-    const int pass = g >= steps;
-    const int t = t_begin + g - pass * steps;
-    const int shift = 4 * pass + q;
-    if (t == t_begin) {
-      left = chunk_left(t, shift);
-      start = true;
-    }
-    const uint32_t G = G0 + (uint32_t)g;
-    const int st = (int)(G % STAGES);
-    const uint32_t ph = (G / STAGES) & 1u;
+  };
+  sl.begin_pass(0, t_begin, tmem);
+  for (int t = t_begin; t < t_end; t += 2) {
     if (!mbar_wait(&gq_full[st], ph, &gq_abort)) return false;
     tc_fence_after();
-    const uint64_t a0 = smem_desc_sw128(stage_base() + st * STAGE_BYTES);
-    const uint64_t b0 = smem_desc_sw128(stage_base() + st * STAGE_BYTES + A_STAGE_BYTES);
-    if (start && chunks > 0) {
-      if (!mbar_wait(&gq_acce[q], (chunks - 1u) & 1u, &gq_abort)) return false;
-      tc_fence_after();
-    }
-    issue_shift(d, a0, b0, shift, start);
-    start = --left == 0 || t == t_end - 1;
-    if (start) {
-      tc_commit(&gq_accf[q]);
-      chunks++;
-      left = chunk_len(shift);
-    }
+    const uint64_t a0 = a_base + (uint64_t)st * STAGE_DESC;
+    const uint64_t b0 = b_base + (uint64_t)st * STAGE_DESC;
+    if (!sl.step(a0, b0, t == t_end - 1, gq_accf, gq_acce, &gq_abort)) return false;
+    if (t + 1 < t_end &&
+        !sl.step(a0 + HALF_DESC, b0 + HALF_DESC, t + 1 == t_end - 1, gq_accf, gq_acce, &gq_abort))
+      return false;
     tc_commit(&gq_empty[st]);
+    next();
+  }
+  sl.begin_pass(1, t_begin, tmem);
+  for (int t = t_begin; t < t_end; ++t) {
+    if (!mbar_wait(&gq_full[st], ph, &gq_abort)) return false;
+    tc_fence_after();
+    const uint64_t a0 = a_base + (uint64_t)st * STAGE_DESC;
+    const uint64_t b0 = b_base + (uint64_t)st * STAGE_DESC;
+    if (!sl.step(a0, b0, t == t_end - 1, gq_accf, gq_acce, &gq_abort)) return false;
+    tc_commit(&gq_empty[st]);
+    next();
   }
   return true;
 }
@@ -768,7 +731,7 @@ __device__ __forceinline__ bool issuer_tile(int q, uint32_t tmem, const TileJob&
 // across tiles.  Returns false on an abort (nothing is written then).
 __device__ __forceinline__ bool drain_tile(uint32_t tmem, const TileJob& jb, uint32_t& parity,
                                            int warp, int lane) {
-  const int ew = warp - kIssuers;               // 0..15
+  const int ew = warp - kDrainBase;             // 0..15
   const int quad = warp & 3;                    // lane quadrant this warp may access
   const int cblk = ew >> 2;                     // which 32 of the 128 columns
   const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cblk * 32);
@@ -1017,44 +980,50 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_grouped_kernel(
   // chunk ends); the CTA barrier at the end of tile k both frees the stage
   // buffers and publishes tile k + 1.
   if (warp < kIssuers) {
+    // ---- MMA issuers: warp q owns accumulator slot q ----
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssuerRegs));
-    TileLoader ldr;
-    for (int i = 0; i < STAGES; ++i) ldr.last_g[i] = -1;
-    uint32_t chunks = 0, G0 = 0;
+    Slot sl{0, warp, 0, 0, 0, true, 0u};
+    int st = 0;
+    uint32_t ph = 0;
     for (int k = 0;; ++k) {
       const int buf = k & 1;
       if (gq_item[buf] >= gp.total) break;
-      const TileJob& jb = gq_job[buf];
-      const int steps = jb.t_end - jb.t_begin;
-      if (lane == 0 && !gq_abort) {
-        if (warp == 0) {
-          for (int pr = 0; pr < 2; ++pr) {
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                             reinterpret_cast<uint64_t>(jb.ta[pr]))
-                         : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                             reinterpret_cast<uint64_t>(jb.tb[pr]))
-                         : "memory");
-          }
-          ldr.start_tile(jb, G0);
-        }
-        issuer_tile(warp, tmem, jb, G0, chunks, warp == 0 ? &ldr : nullptr);
-      }
-      G0 += 2u * (uint32_t)steps;
+      if (lane == 0 && !gq_abort) mma_tile(sl, tmem, gq_job[buf], st, ph);
       __syncwarp();
       asm volatile("bar.sync 2, %0;" ::"r"(kThreads) : "memory");  // tile done, next published
     }
-    if (lane == 0) {
-      if (warp == 0) ldr.drain_copies();
-      issuer_finish();
+    if (lane == 0) issuer_finish();
+  } else if (warp < kDrainBase) {
+    // ---- the producer (one thread of warp 4) ----
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+    int st = 0, n = 0;
+    uint32_t ph = 0;
+    for (int k = 0;; ++k) {
+      const int buf = k & 1;
+      if (gq_item[buf] >= gp.total) break;
+      if (warp == kProducerWarp && lane == 0 && !gq_abort) {
+        const TileJob& jb = gq_job[buf];
+        for (int pr = 0; pr < 2; ++pr) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                           reinterpret_cast<uint64_t>(jb.ta[pr]))
+                       : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                           reinterpret_cast<uint64_t>(jb.tb[pr]))
+                       : "memory");
+        }
+        producer_tile(jb, st, ph, n);
+      }
+      __syncwarp();
+      asm volatile("bar.sync 2, %0;" ::"r"(kThreads) : "memory");
     }
+    if (warp == kProducerWarp && lane == 0) drain_copies(n, gq_full);
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs));
     uint32_t parity = 0;
     for (int k = 0;; ++k) {
       const int buf = k & 1;
       if (gq_item[buf] >= gp.total) break;
-      if (warp == kIssuers && lane == 0) claim(buf ^ 1);
+      if (warp == kDrainBase && lane == 0) claim(buf ^ 1);
       __syncwarp();
       // Always entered: drain_tile's named barrier needs all 16 drain warps
       // (after an abort its waits give up at once and nothing is written).
@@ -1535,7 +1504,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(g.njobs * g.splits));
   {
     KernelTimer timer("gemm_limb", s);
-    limb_gemm_kernel<<<grid, kOneThreads, SMEM_BYTES, s>>>(prm);
+    limb_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(prm);
     if (int rc = check_launch("gemm_limb")) return rc;
   }
   return (g.splits > 1 && !g.defer_reduce) ? gemm_reduce(g, s) : MPC_OK;
