@@ -96,6 +96,7 @@ constexpr int kProducerWarp = 4;   // TMA loads (one thread)
 constexpr int kDrainBase = 8;      // first TMEM drain / epilogue warp
 constexpr int kDrainWarps = 16;
 constexpr int kWarps = kDrainBase + kDrainWarps, kThreads = 32 * kWarps;
+static_assert(BM % kDrainWarps == 0, "epilogue rows split evenly over the drain warps");
 // Launched with 80 registers per thread (768 threads); after launch
 // (setmaxnreg) the MMA warpgroup keeps 40, the producer warpgroup 24 and the
 // drain warpgroups take 104, enough to hold a slot's 32 drained columns beside
@@ -112,6 +113,11 @@ static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "epilogue tile fits the
 // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
+// The same with N = 64: a grouped tile with at most 64 columns left in its
+// product runs half-width MMAs (the accumulator's other 64 columns are never
+// written and never stored).
+constexpr uint32_t IDESC_N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                               ((uint32_t)(BM >> 4) << 24);
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 // Each operand pair has its own planes ([rows][K1p / 16][8][16], K1p = K
@@ -209,11 +215,11 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t accumulate) {
+                                       uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
@@ -249,9 +255,10 @@ __device__ __forceinline__ void tmem_wait_ld() {
 
 // The s + 1 digit-pair MMAs of shift s: D += sum_{i <= s} A_i B_{s - i}.
 __device__ __forceinline__ void issue_shift(uint32_t d, uint64_t a0, uint64_t b0, int s,
-                                            bool start) {
-  tc_mma(d, a0, b0 + plane_desc_off(s), start ? 0u : 1u);
-  for (int i = 1; i <= s; ++i) tc_mma(d, a0 + plane_desc_off(i), b0 + plane_desc_off(s - i), 1u);
+                                            bool start, uint32_t idesc) {
+  tc_mma(d, a0, b0 + plane_desc_off(s), idesc, start ? 0u : 1u);
+  for (int i = 1; i <= s; ++i)
+    tc_mma(d, a0 + plane_desc_off(i), b0 + plane_desc_off(s - i), idesc, 1u);
 }
 
 // Chunk length of shift s in sub-steps of K = 16: the shift sums the s + 1
@@ -342,6 +349,7 @@ struct Slot {
   int q, shift, len, left;
   bool start;
   uint32_t chunks;  // chunks committed so far
+  uint32_t idesc;   // instruction descriptor: N = 128, or 64 for a narrow grouped tile
   __device__ __forceinline__ void begin_pass(int pass, int t_begin, uint32_t tmem) {
     d = tmem + (uint32_t)(q * BN);
     shift = 4 * pass + q;
@@ -356,7 +364,7 @@ struct Slot {
       if (!mbar_wait(&acce_bar[q], (chunks - 1u) & 1u, abort_flag)) return false;
       tc_fence_after();
     }
-    issue_shift(d, a0, b0, shift, start);
+    issue_shift(d, a0, b0, shift, start, idesc);
     start = --left == 0 || last;
     if (start) {
       tc_commit(&accf_bar[q]);
@@ -374,7 +382,7 @@ __device__ __forceinline__ void mma_loop(int q, uint32_t sbase, uint32_t tmem, i
                                          int t_end, uint64_t* full_bar, uint64_t* empty_bar,
                                          uint64_t* accf_bar, uint64_t* acce_bar,
                                          volatile int* abort_flag) {
-  Slot sl{0, q, 0, 0, 0, true, 0u};
+  Slot sl{0, q, 0, 0, 0, true, 0u, IDESC};
   const uint64_t a_base = smem_desc_sw128(sbase);
   const uint64_t b_base = smem_desc_sw128(sbase + A_STAGE_BYTES);
   constexpr uint64_t HALF_DESC = HALF_LOAD_BYTES >> 4;
@@ -689,6 +697,7 @@ __device__ __forceinline__ bool producer_tile(const TileJob& jb, int& st, uint32
 // abort.
 __device__ __forceinline__ bool mma_tile(Slot& sl, uint32_t tmem, const TileJob& jb, int& st,
                                          uint32_t& ph) {
+  sl.idesc = jb.N - jb.n0 <= 64 ? IDESC_N64 : IDESC;
   const int t_begin = jb.t_begin, t_end = jb.t_end;
   const uint32_t sbase = stage_base();
   const uint64_t a_base = smem_desc_sw128(sbase);
@@ -818,31 +827,48 @@ __device__ __forceinline__ bool drain_tile(uint32_t tmem, const TileJob& jb, uin
   // pointers could alias the shared-memory job and would force reloads.
   const i64 M = jb.M, N = jb.N, hw_out = jb.hw_out;
   const int m0 = jb.m0, n0 = jb.n0, trunc_bits = jb.trunc_bits;
-  const u64* C = jb.C;
-  u64* Z = jb.Z;
+  const u64* __restrict__ C = jb.C;
+  u64* __restrict__ Z = jb.Z;
   u64* part0 = jb.part;
-  for (int r = ew; r < BM; r += kDrainWarps) {
-    const i64 row = (i64)m0 + r;
-    if (row >= M) break;
-    const u64* src = stile + r * SROW;
-    if (part0) {
+  constexpr int ROWS = BM / kDrainWarps, COLS = BN / 32;  // 8 rows of 4 x 32 columns per warp
+  if (part0) {
+    for (int r = ew; r < BM; r += kDrainWarps) {
+      const i64 row = (i64)m0 + r;
+      if (row >= M) break;
+      const u64* src = stile + r * SROW;
       u64* part = part0 + row * N;
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) {
+      for (int k = 0; k < COLS; ++k) {
         const int c = 32 * k + lane;
         if ((i64)n0 + c < N) part[n0 + c] = src[c];
       }
-    } else {
+    }
+  } else {
+    // Every C word of the warp's rows is requested before the first store, so
+    // their latencies overlap (row by row, each store waited for its load).
+    u64 cv[ROWS][COLS];
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) {
+    for (int i = 0; i < ROWS; ++i) {
+      const i64 row = (i64)m0 + ew + i * kDrainWarps;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        const i64 col = (i64)n0 + 32 * k + lane;
+        cv[i][k] = (C && row < M && col < N) ? C[gemm_out_index(row, col, M, N, hw_out)] : 0ull;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+      const int r = ew + i * kDrainWarps;
+      const i64 row = (i64)m0 + r;
+      const u64* src = stile + r * SROW;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
         const int c = 32 * k + lane;
         const i64 col = (i64)n0 + c;
-        if (col < N) {
-          const i64 idx = gemm_out_index(row, col, M, N, hw_out);
-          u64 v = src[c];
-          if (C) v += C[idx];
+        if (row < M && col < N) {
+          u64 v = src[c] + cv[i][k];
           if (trunc_bits > 0) v = sar(v, trunc_bits);
-          Z[idx] = v;
+          Z[gemm_out_index(row, col, M, N, hw_out)] = v;
         }
       }
     }
@@ -982,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_grouped_kernel(
   if (warp < kIssuers) {
     // ---- MMA issuers: warp q owns accumulator slot q ----
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssuerRegs));
-    Slot sl{0, warp, 0, 0, 0, true, 0u};
+    Slot sl{0, warp, 0, 0, 0, true, 0u, IDESC};
     int st = 0;
     uint32_t ph = 0;
     for (int k = 0;; ++k) {
@@ -1252,23 +1278,98 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
 // nparty > 0 the source is opened on the fly: element i is
 // sum_p (src[p][i] - sub[p][i]) (+ add[i]), party p at p * pstride.  A B-side
 // task with out2 also writes the planes of that element plus add2[i] to out2.
+// A side of a Beaver product, from one read of X and A: the opened
+// E = sum_p (X_p - A_p) and every party's A_p, each cut into digit planes
+// ([M][K] row-major sources, parties pstride words apart); E's planes go to
+// out, A_p's to out + (1 + p) ostride.  Block `blk` of `nblk` strides over the
+// 8-k groups.
+__device__ __forceinline__ void planes_a_beaver(const u64* __restrict__ X,
+                                                const u64* __restrict__ S, i64 pstride, int P,
+                                                __nv_bfloat16* out, i64 ostride, i64 M, i64 K,
+                                                i64 Kp, i64 blk, i64 nblk) {
+  const i64 kc = Kp / 8;
+  const i64 total = M * kc;
+  for (i64 i = blk * (i64)blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
+    const i64 m = i / kc, k0 = (i % kc) * 8;
+    u64 e[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) e[j] = 0;
+    for (int p = 0; p < P; ++p) {
+      u64 a[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const i64 k = k0 + j;
+        a[j] = 0;
+        if (k < K) {
+          const i64 idx = p * pstride + m * K + k;
+          a[j] = S[idx];
+          e[j] += X[idx] - a[j];
+        }
+      }
+      write_planes(a, out + (1 + p) * ostride, m, Kp, k0);
+    }
+    write_planes(e, out, m, Kp, k0);
+  }
+}
+
+// B side of a Beaver product, K-major like planes_b_kmajor, from one read of
+// Y and B: F = sum_p (Y_p - B_p), G = B_0 + F and B_1 .. B_{P-1} ([K][N]
+// row-major sources, parties pstride words apart); G's planes go to out, B_p's
+// to out + p ostride, F's to out + P ostride.
+__device__ __forceinline__ void planes_b_beaver(const u64* __restrict__ Y,
+                                                const u64* __restrict__ S, i64 pstride, int P,
+                                                __nv_bfloat16* out, i64 ostride, i64 N, i64 K,
+                                                i64 Kp, int bx, int by) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const i64 t = (i64)bx * 8 + w;
+  const i64 n = (i64)by * 16 + (l >> 1);
+  if (t >= Kp / KS || n >= N) return;
+  const i64 k0 = t * KS + (l & 1) * 8;
+  u64 f[8], b0[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) f[j] = 0;
+  for (int p = 0; p < P; ++p) {
+    u64 b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      b[j] = 0;
+      if (k0 + j < K) {
+        const i64 idx = p * pstride + (k0 + j) * N + n;
+        b[j] = S[idx];
+        f[j] += Y[idx] - b[j];
+      }
+    }
+    if (p == 0) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b0[j] = b[j];
+    } else {
+      write_planes(b, out + p * ostride, n, Kp, k0);
+    }
+  }
+  write_planes(f, out + P * ostride, n, Kp, k0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) f[j] += b0[j];
+  write_planes(f, out, n, Kp, k0);
+}
+
+// One side of one product of a grouped launch: the planes of its P + 1
+// sources (side 0: E, A_0 .. A_{P-1}; side 1: G, B_1 .. B_{P-1}, F), which
+// sit ostride bf16 apart from out in map order.
 struct __align__(16) PlaneTask {
-  const u64* src;
-  const u64* sub;
-  const u64* add;
-  const u64* add2;
+  const u64* src;  // X or Y
+  const u64* sub;  // A or B
   __nv_bfloat16* out;
-  __nv_bfloat16* out2;
+  i64 ostride;
   i64 rows, K, Kp;
   i64 block_base;
   i64 pstride;
-  int side;    // 0: A side, 1: B side (transposed)
-  int nblk;    // blocks of this task
-  int bx;      // B side: tiles of 64 k
-  int nparty;  // 0: direct source
+  int side;  // 0: A side, 1: B side (transposed)
+  int nblk;  // blocks of this task
+  int bx;    // B side: tiles of 8 sub-steps
+  int P;
 };
 
-__global__ void __launch_bounds__(256) limb_planes_grouped(const PlaneTask* __restrict__ tasks,
+__global__ void __launch_bounds__(256, 3) limb_planes_grouped(const PlaneTask* __restrict__ tasks,
                                                            int ntasks) {
   const i64 b = blockIdx.x;
   int lo = 0, hi = ntasks - 1;
@@ -1278,20 +1379,12 @@ __global__ void __launch_bounds__(256) limb_planes_grouped(const PlaneTask* __re
   }
   const PlaneTask& t = tasks[lo];
   const i64 local = b - t.block_base;
-  const int bx = (int)(local % t.bx), by = (int)(local / t.bx);
-  if (t.nparty == 0) {
-    const DirectSrc src{t.src};
-    if (t.side == 0)
-      planes_a_part(src, t.out, t.rows, t.K, t.Kp, local, t.nblk);
-    else
-      planes_b_kmajor(src, nullptr, t.out, nullptr, t.rows, t.K, t.Kp, bx, by);
-  } else {
-    const OpenedSrc src{t.src, t.sub, t.add, t.pstride, t.nparty};
-    if (t.side == 0)
-      planes_a_part(src, t.out, t.rows, t.K, t.Kp, local, t.nblk);
-    else
-      planes_b_kmajor(src, t.add2, t.out, t.out2, t.rows, t.K, t.Kp, bx, by);
-  }
+  if (t.side == 0)
+    planes_a_beaver(t.src, t.sub, t.pstride, t.P, t.out, t.ostride, t.rows, t.K, t.Kp, local,
+                    t.nblk);
+  else
+    planes_b_beaver(t.src, t.sub, t.pstride, t.P, t.out, t.ostride, t.rows, t.K, t.Kp,
+                    (int)(local % t.bx), (int)(local / t.bx));
 }
 
 // Copies a block of kernel parameters to device memory: how the grouped
@@ -1589,45 +1682,33 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
     const i64 K1p = pair_k(g.K);
     const size_t a_bytes = al256((size_t)16 * g.M * K1p), b_bytes = al256((size_t)16 * g.N * K1p);
     // Sources in map order: A side E, A_0..A_{P-1}; B side G, B_1..B_{P-1},
-    // F.  E = sum_p (X_p - A_p) and F = sum_p (Y_p - B_p) are opened inside
-    // the plane pass; one task writes both F and G = B_0 + F.
+    // F, each side's planes consecutive.  One task per side cuts all of them
+    // from one read of the shares (E = sum_p (X_p - A_p) and
+    // F = sum_p (Y_p - B_p) are opened inside the pass, G = B_0 + F).
     const i64 mk = g.M * g.K, kn = g.K * g.N;
-    __nv_bfloat16* g_planes = nullptr;
-    for (int m = 0; m < nmaps; ++m) {
-      const bool aside = m <= P;
-      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(planes);
-      planes += aside ? a_bytes : b_bytes;
+    for (int side = 0; side < 2; ++side) {
+      const bool aside = side == 0;
       const i64 rows = aside ? g.M : g.N;
-      if (int rc = encode_planes(&hm[(size_t)i * nmaps + m], out, rows, K1p, aside ? BM : BN))
-        return rc;
-      if (m == P + 1) {  // G: written by F's task
-        g_planes = out;
-        continue;
+      const size_t bytes = aside ? a_bytes : b_bytes;
+      __nv_bfloat16* first = reinterpret_cast<__nv_bfloat16*>(planes);
+      for (int j = 0; j <= P; ++j) {
+        const int m = aside ? j : P + 1 + j;
+        if (int rc = encode_planes(&hm[(size_t)i * nmaps + m], planes, rows, K1p, aside ? BM : BN))
+          return rc;
+        planes += bytes;
       }
       PlaneTask t{};
-      if (m == 0) {
-        t.src = g.X;
-        t.sub = g.A;
-        t.pstride = mk;
-        t.nparty = P;
-      } else if (aside) {
-        t.src = g.A + (i64)(m - 1) * mk;
-      } else if (m == 2 * P + 1) {
-        t.src = g.Y;
-        t.sub = g.B;
-        t.pstride = kn;
-        t.nparty = P;
-        t.add2 = g.B;      // party 0's B: G = B_0 + F
-        t.out2 = g_planes;
-      } else {
-        t.src = g.B + (i64)(m - P - 1) * kn;
-      }
-      t.out = out;
+      t.src = aside ? g.X : g.Y;
+      t.sub = aside ? g.A : g.B;
+      t.pstride = aside ? mk : kn;
+      t.P = P;
+      t.out = first;
+      t.ostride = (i64)(bytes / sizeof(__nv_bfloat16));
       t.rows = rows;
       t.K = g.K;
       t.Kp = K1p;
       t.block_base = block_base;
-      t.side = aside ? 0 : 1;
+      t.side = side;
       if (aside) {
         t.nblk = (int)std::min<i64>(ceil_div(g.M * (K1p / 8), 256), 148 * 4);
       } else {  // blocks of 8 sub-steps x 16 columns
