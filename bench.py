@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 # speech step (7 dealer GEMMs of one operand pair, 7 online GEMMs of two pairs
 # for two parties), from an ncu capture of dram__bytes_read.sum +
 # dram__bytes_write.sum on the current kernel.
-LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 59.4e6
+LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 59.3e6
 REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
 
 
