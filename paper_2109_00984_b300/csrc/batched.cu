@@ -298,19 +298,22 @@ int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int tru
     mpc_tune t = default_tune();
     t.limb_min_macs = c;
     if (make_plan(P, count, descs, MPC_ALGO_AUTO, t).total > ws_bytes) continue;
-    float ms_sum = 0.f;
-    for (int rep = 0; rep < 3 && rc == MPC_OK; ++rep) {
+    // The fastest of four timed runs after one warm-up: the minimum is the
+    // candidate's own time, least disturbed by whatever else shares the GPU
+    // (with a mean of two, noise picked thresholds that were 5-10 % slower).
+    float ms_min = -1.f;
+    for (int rep = 0; rep < 5 && rc == MPC_OK; ++rep) {
       cudaEventRecord(e0, s);
       rc = run_batched(P, count, descs, MPC_ALGO_AUTO, t, trunc_bits, ws, ws_bytes, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(MPC_ECUDA, "autotune sync failed");
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_sum += ms;  // the first run warms up
+      if (rep > 0 && (ms_min < 0.f || ms < ms_min)) ms_min = ms;
     }
     if (rc != MPC_OK) break;
-    if (best_ms < 0.f || ms_sum < best_ms) {
-      best_ms = ms_sum;
+    if (best_ms < 0.f || ms_min < best_ms) {
+      best_ms = ms_min;
       best = t;
     }
   }
