@@ -574,6 +574,35 @@ def measure_ring_gemm(n, algo, dev, reps, flush, bf16_burst):
     return rec
 
 
+def measure_beaver3(n, algo, dev, reps, flush):
+    """The three-party Beaver online step on an n x n x n product (SURVEY config 3 (ii)):
+    opening of E and F, then per party one ring GEMM over the K-concatenated pairs
+    [E | A_p] [B_p (+ F) ; F] (K' = 2n), plus C_p and the truncation; triples dealt
+    beforehand.  Ring ops = 2 x 3 parties x n^2 x 2n."""
+    import torch
+
+    import paper_2109_00984_b300 as mpc
+    P = 3
+    g = torch.Generator(device=dev)
+    g.manual_seed(n + 3)
+    X = torch.randint(-2 ** 63, 2 ** 63 - 1, (P, n, n), dtype=torch.int64, device=dev, generator=g)
+    Y = torch.randint(-2 ** 63, 2 ** 63 - 1, (P, n, n), dtype=torch.int64, device=dev, generator=g)
+    A, B, C = mpc.ttp_matmul_triple(P, n, n, n, 1, 70000 + n, algo=mpc.LIMB, device=dev)
+    Z = torch.empty((P, n, n), dtype=torch.int64, device=dev)
+    ws = torch.empty(max(1, mpc.matmul_workspace_size(P, n, n, n, algo)), dtype=torch.uint8,
+                     device=dev)
+
+    def call():
+        mpc.beaver_matmul(X, Y, A, B, C, algo=algo, trunc_bits=16, out=Z, ws=ws)
+
+    ms = median_event_ms(call, reps, flush)
+    ring_ops = 2.0 * P * n * n * 2 * n
+    rec = {"ms": ms, "ring_tops": ring_ops / (ms / 1e3) / 1e12, "reps": reps}
+    del X, Y, A, B, C, Z, ws
+    torch.cuda.empty_cache()
+    return rec
+
+
 def extra_gemm_sweep(dev, peaks, sizes=(4096, 8192), reps=5):
     """Limb (tcgen05) vs plain (CUDA-core) ring GEMM at the largest sweep sizes."""
     import torch
@@ -590,6 +619,15 @@ def extra_gemm_sweep(dev, peaks, sizes=(4096, 8192), reps=5):
         limb = measure_ring_gemm(n, mpc.LIMB, dev, reps, flush, burst)
         plain = measure_ring_gemm(n, mpc.PLAIN, dev, max(2, reps // 2), flush, burst)
         out[str(n)] = {"limb": limb, "plain": plain, "limb_over_plain": plain["ms"] / limb["ms"]}
+    # The three-party Beaver online step at the first size, both engines.
+    n = sizes[0]
+    b_limb = measure_beaver3(n, mpc.LIMB, dev, reps, flush)
+    b_plain = measure_beaver3(n, mpc.PLAIN, dev, 2, flush)
+    out[f"beaver3_{n}"] = {"workload": "three-party Beaver matmul online step (E, F opened, "
+                                       "per party one two-pair ring GEMM, K' = 2n, C and "
+                                       "truncation), triples dealt beforehand",
+                           "limb": b_limb, "plain": b_plain,
+                           "limb_over_plain": b_plain["ms"] / b_limb["ms"]}
     del flush
     torch.cuda.empty_cache()
     return out
@@ -700,6 +738,7 @@ def run_gemm_sweep(args):
                 rec["tensor_tflops"] = tf
                 rec["tensor_frac_of_bf16_burst"] = tf / bf16
             out[f"{name}_{n}"] = rec
+            out[f"beaver3_{name}_{n}"] = measure_beaver3(n, algo, dev, min(reps, 3), flush)
             del ws
         del A, B, Z
         torch.cuda.empty_cache()

@@ -337,7 +337,10 @@ int mpc_beaver_matmul_batched(int P, int count, const mpc_matmul_desc* descs, in
 
 /* Autotuner: times the batched call (algo AUTO) for limb thresholds from
  * "never" through 2^32 .. 2^16 ring MACs to "always" (each candidate the
- * fastest of four calls after one warm-up) and returns the fastest in *out.
+ * fastest of four calls after one warm-up, with L2 evicted before each call by
+ * overwriting up to 256 MB of ws, and device time only: each timed call waits
+ * behind a 20 ms device delay while the host enqueues it) and returns the
+ * fastest in *out.
  * Synchronises `stream`; not for use inside stream capture.  Writes Z. */
 int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int trunc_bits,
                          void* ws, size_t ws_bytes, void* stream, mpc_tune* out);

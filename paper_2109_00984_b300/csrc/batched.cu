@@ -30,6 +30,17 @@ struct TableChunk {
   int offset;
 };
 
+// One thread idles on the global timer for `ns` nanoseconds (the wait ends by
+// itself): the autotuner enqueues it ahead of a timed call so that the host has
+// enqueued the whole call before the GPU reaches the call's start event.
+__global__ void delay_kernel(unsigned long long ns) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  do {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  } while (t - t0 < ns);
+}
+
 __global__ void table_write_kernel(const TableChunk chunk, BatchProd* tbl) {
   const int i = threadIdx.x;
   if (i < chunk.count) tbl[chunk.offset + i] = chunk.items[i];
@@ -300,9 +311,19 @@ int mpc_autotune_batched(int P, int count, const mpc_matmul_desc* descs, int tru
     if (make_plan(P, count, descs, MPC_ALGO_AUTO, t).total > ws_bytes) continue;
     // The fastest of four timed runs after one warm-up: the minimum is the
     // candidate's own time, least disturbed by whatever else shares the GPU
-    // (with a mean of two, noise picked thresholds that were 5-10 % slower).
+    // (timing host work and warm operands with a mean of two picked
+    // thresholds that were 5-10 % slower as graph replays on cold operands).
     float ms_min = -1.f;
     for (int rep = 0; rep < 5 && rc == MPC_OK; ++rep) {
+      // Evict the previous call's operands from L2 (126 MB) by overwriting up
+      // to 256 MB of the workspace, which every batched call rewrites before
+      // it reads: each candidate is timed as a call on cold operands.
+      if (cudaMemsetAsync(ws, 0, std::min<size_t>(ws_bytes, (size_t)256 << 20), s) != cudaSuccess)
+        rc = fail(MPC_ECUDA, "autotune L2 eviction failed");
+      // 20 ms of device idling covers the host's plan and tensor-map encoding,
+      // so the events time the device work alone (as a CUDA-graph replay of
+      // the call would run) instead of favouring plans with less host work.
+      delay_kernel<<<1, 1, 0, s>>>(20000000ull);
       cudaEventRecord(e0, s);
       rc = run_batched(P, count, descs, MPC_ALGO_AUTO, t, trunc_bits, ws, ws_bytes, s);
       cudaEventRecord(e1, s);
