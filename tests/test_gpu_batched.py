@@ -169,3 +169,26 @@ def test_uneven_512_batch_sampled(mpc):
     bm()
     mpc.sync_status()
     check("all limb")
+
+
+@pytest.mark.parametrize("P", [2, 3])
+def test_batched_narrow_edge_tiles(mpc, P, rng):
+    """Column counts whose last 128-column tile has at most 64 columns (the
+    persistent kernel runs those tiles with N = 64 MMAs) or just over 64, with K
+    odd in 16-steps so that the last pass-0 stage holds a single sub-step."""
+    dims = np.array([(130, 64, 48), (257, 65, 80), (96, 192, 112), (140, 200, 16),
+                     (64, 129, 272), (200, 320, 208), (33, 1, 144)])
+    prods, refs = [], []
+    for i, (M, N, K) in enumerate(dims):
+        X = rng.integers(0, 2 ** 64, (P, M, K), dtype=np.uint64)
+        Y = rng.integers(0, 2 ** 64, (P, K, N), dtype=np.uint64)
+        A, B, C = dealer.matmul_triple(P, M, N, K, SEED, 900 + i)
+        prods.append((X, Y, A, B, C))
+        refs.append(truncation.truncate(beaver.beaver_matmul(X, Y, A, B, C), 16))
+    dprods = _to_dev(prods, P)
+    tune = mpc.default_tune()
+    tune.limb_ctas = 5
+    mpc.beaver_matmul_batched(dprods, algo=mpc.LIMB, trunc_bits=16, tune=tune)
+    mpc.sync_status()
+    for i, (d, r) in enumerate(zip(dprods, refs)):
+        assert np.array_equal(host(d[5]), r), f"product {i} dims {dims[i]}"
