@@ -393,6 +393,20 @@ def run_ours(args):
                           "forward's dealing, each alone as a graph replay; the timed steps "
                           "overlap the two on two streams"}
         del g_on, g_deal
+        # The same with the convolutions' input-independent half (F = W - B
+        # opened, weight-side and im2col(A_p) planes) moved to the dealer: the
+        # online phase's latency, not used for the throughput steps above.
+        net.enable_prepared(True)
+        if net.prepared:
+            net.deal(sch, 0, join=True)
+            g_on = phase_graph(lambda: net.reveal(net.online(x_dev, sch, 0, wait_dealer=False)))
+            g_deal = phase_graph(lambda: net.deal(sch, 1, join=True))
+            phases["online_only_prepared_ms"] = median_event_ms(g_on.replay, args.steps, flush,
+                                                                warm=2)
+            phases["dealer_only_prepared_ms"] = median_event_ms(g_deal.replay, args.steps, flush,
+                                                                warm=2)
+            del g_on, g_deal
+        net.enable_prepared(False)
 
     if rank != 0:
         if world > 1:

@@ -266,6 +266,36 @@ int mpc_beaver_conv2d_relu(int P, const mpc_conv_desc* d, const uint64_t* X, con
                            int algo, int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
                            size_t ws_bytes, void* stream);
 
+/* Input-independent half of a Beaver convolution on the limb engine (App.
+ * D.1.1: F = W - B does not depend on the data, so it can be opened as soon as
+ * the triple is dealt; the regrouping of the product is the one of
+ * mpc_beaver_conv2d).  Opens F = sum_p (W_p - B_p) and cuts into prep the
+ * digit planes of G = B_0 + F, B_1 .. B_{P-1}, F and of im2col(A_p) for every
+ * party (the GEMM operands that do not involve X).  W, A, B as for
+ * mpc_beaver_conv2d (device, read only); prep: caller-owned device buffer of
+ * mpc_conv2d_prep_size() bytes (0 = shape or party count not supported: the
+ * limb engine's shape limits), written, read by the prepared call below.
+ * Counts one round and the F bytes opened.  MPC_ENOMEM if prep_bytes is too
+ * small; no workspace. */
+size_t mpc_conv2d_prep_size(int P, const mpc_conv_desc* d);
+int mpc_beaver_conv2d_prepare(int P, const mpc_conv_desc* d, const uint64_t* W, const uint64_t* A,
+                              const uint64_t* B, void* prep, size_t prep_bytes, void* stream);
+
+/* The data-dependent half: opens E = sum_p (X_p - A_p), gathers im2col(E) into
+ * digit planes and runs the limb-engine GEMM on them and the prepared planes
+ * (the same triple A as the prepare call).  Results equal mpc_beaver_conv2d /
+ * mpc_beaver_conv2d_relu with algo = MPC_ALGO_LIMB bit for bit.  ws as
+ * mpc_conv2d_workspace_size(P, d, MPC_ALGO_LIMB).  The ReLU variant needs
+ * P = 2 (material at relu_op .. relu_op + 3). */
+int mpc_beaver_conv2d_prepared(int P, const mpc_conv_desc* d, const uint64_t* X,
+                               const uint64_t* A, const uint64_t* C, const void* prep,
+                               size_t prep_bytes, uint64_t* Z, int trunc_bits, void* ws,
+                               size_t ws_bytes, void* stream);
+int mpc_beaver_conv2d_relu_prepared(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                    const uint64_t* A, const uint64_t* C, const void* prep,
+                                    size_t prep_bytes, uint64_t* Y, int trunc_bits, uint64_t seed,
+                                    uint64_t relu_op, void* ws, size_t ws_bytes, void* stream);
+
 /* Beaver matmul that allocates nothing (the paper has no counterpart: this is
  * an interface for callers that can neither allocate device memory when they
  * call the library nor hand it a workspace, e.g. a host program whose device

@@ -225,6 +225,59 @@ def beaver_conv2d(X, W, A, B, C, d, algo=PLAIN, trunc_bits=0, out=None, ws=None)
     return Z
 
 
+def conv2d_prep_size(P, d):
+    """Bytes of the prepared-plane buffer of a limb-engine Beaver convolution (0: unsupported)."""
+    return _L().mpc_conv2d_prep_size(P, ctypes.byref(d))
+
+
+def beaver_conv2d_prepare(W, A, B, d, out=None):
+    """Input-independent half of a limb-engine Beaver convolution: opens F = W - B and cuts
+    the digit planes of the weight side and of im2col(A_p) into a uint8 device buffer
+    (returned), to be passed to beaver_conv2d_prepared / beaver_conv2d_relu_prepared with
+    the same triple."""
+    P = W.shape[0]
+    need = conv2d_prep_size(P, d)
+    if need == 0:
+        raise MPCError(-6, "no prepared planes for this convolution shape")
+    prep = torch.empty(need, dtype=torch.uint8, device=W.device) if out is None else out
+    _check(_L().mpc_beaver_conv2d_prepare(P, ctypes.byref(d), _ptr(W), _ptr(A), _ptr(B),
+                                          _ptr(prep, "prep", torch.uint8), prep.numel(),
+                                          _stream()))
+    return prep
+
+
+def beaver_conv2d_prepared(X, A, C, prep, d, trunc_bits=0, out=None, ws=None):
+    """Data-dependent half of a limb-engine Beaver convolution on prepared planes;
+    equals beaver_conv2d(..., algo=LIMB)."""
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Z = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), LIMB)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_prepared(P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(C),
+                                           _ptr(prep, "prep", torch.uint8), prep.numel(), _ptr(Z),
+                                           trunc_bits, _ptr(ws, "ws", torch.uint8), ws.numel(),
+                                           _stream()))
+    return Z
+
+
+def beaver_conv2d_relu_prepared(X, A, C, prep, d, seed, relu_op, trunc_bits=0, out=None,
+                                ws=None):
+    """beaver_conv2d_prepared then the fused private ReLU (two parties); equals
+    beaver_conv2d_relu(..., algo=LIMB)."""
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Y = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), LIMB)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_relu_prepared(P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(C),
+                                                _ptr(prep, "prep", torch.uint8), prep.numel(),
+                                                _ptr(Y), trunc_bits, seed, relu_op,
+                                                _ptr(ws, "ws", torch.uint8), ws.numel(),
+                                                _stream()))
+    return Y
+
+
 def beaver_conv2d_relu(X, W, A, B, C, d, seed, relu_op, algo=PLAIN, trunc_bits=0, out=None,
                        ws=None):
     """Beaver convolution then the fused private ReLU (material at relu_op .. relu_op + 3),

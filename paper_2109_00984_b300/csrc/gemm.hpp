@@ -49,6 +49,11 @@ struct GemmArgs {
   int defer_reduce;
   u64* partial;
   const ConvGather* gather;  // host pointer; when set, B1/B2 are implicit im2col (limb only)
+  // Limb engine, convolution with gather only: digit planes cut ahead of the
+  // call by limb_conv_prepare (layout in its comment).  The A operands and
+  // every job's B2 are taken from there; only the opened gather B1 is cut in
+  // the call.  jobs[j].A1 / A2 / B2 are then unused.
+  const void* prep;
   GemmJob jobs[MPC_MAX_PARTIES];
 };
 
@@ -101,6 +106,17 @@ int plain_tiles(i64 M, i64 N, i64* tm, i64* tn);
 // count.  Partial sums for split-K live in g.partial (sized by the caller).
 size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs);
 int launch_gemm_limb(const GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t s);
+
+// The input-independent digit planes of a P-party Beaver convolution on the
+// limb engine (M = c_out, K = c_in kh kw, N = batch ho wo): the planes of the
+// P + 1 weight-side sources asrc = G = B_0 + F, B_1 .. B_{P-1}, F ([M][K]
+// row-major operands of the GEMM's A side), then those of im2col(A_p) for
+// p = 0 .. P-1 (B side, gathered from cg.src2), each plane set
+// al256(16 rows K1p) bytes, K1p = K rounded up to 16.  prep must hold
+// limb_conv_prep_bytes(P, M, N, K) bytes.
+size_t limb_conv_prep_bytes(int P, i64 M, i64 N, i64 K);
+int limb_conv_prepare(int P, const ConvGather& cg, i64 M, i64 N, i64 K,
+                      const u64* const* asrc, void* prep, cudaStream_t s);
 bool limb_supported(i64 M, i64 N, i64 K);
 
 // Grouped limb engine: the Beaver products of a batch in one digit-plane launch

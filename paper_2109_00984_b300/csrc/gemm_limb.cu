@@ -1250,6 +1250,7 @@ struct PlanesLaunch {
   ConvGather cg;
   i64 M, N, K, Kp;
   int na, a_blk, nb, bx, by;
+  int z0;  // B side: first output index (gather z0 .. z0 + nb - 1)
 };
 
 // B-side blocks cover 8 sub-steps x 16 columns (bx x by per source), from
@@ -1264,7 +1265,7 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
     return;
   }
   const int r = (int)(b - a_blocks);
-  const int bx = r % pl.bx, by = (r / pl.bx) % pl.by, z = r / (pl.bx * pl.by);
+  const int bx = r % pl.bx, by = (r / pl.bx) % pl.by, z = pl.z0 + r / (pl.bx * pl.by);
   if (GATHER)
     planes_b_conv_kmajor(pl.cg, pl.jb, (int)pl.N, (int)pl.K, (int)pl.Kp, bx, by, z);
   else
@@ -1474,6 +1475,51 @@ size_t limb_workspace_bytes(i64 M, i64 N, i64 K, int npairs, int njobs) {
   return (size_t)njobs * npairs * (al256((size_t)8 * M * K1p * 2) + al256((size_t)8 * N * K1p * 2));
 }
 
+size_t limb_conv_prep_bytes(int P, i64 M, i64 N, i64 K) {
+  const i64 K1p = pair_k(K);
+  return (size_t)(P + 1) * al256((size_t)16 * M * K1p) + (size_t)P * al256((size_t)16 * N * K1p);
+}
+
+int limb_conv_prepare(int P, const ConvGather& cg, i64 M, i64 N, i64 K,
+                      const u64* const* asrc, void* prep, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return MPC_OK;
+  const i64 K1p = pair_k(K);
+  const size_t a_bytes = al256((size_t)16 * M * K1p), b_bytes = al256((size_t)16 * N * K1p);
+  char* w = static_cast<char*>(prep);
+  const mpc_conv_desc& d = cg.d;
+  const i64 data = d.batch * d.c_in * d.h * d.w;
+  if (data >= (1ll << 31) || N >= (1ll << 31) || K1p >= (1ll << 31) ||
+      (i64)8 * N * K1p >= (1ll << 62))
+    return fail(MPC_EUNSUPPORTED, "convolution too large for the 32-bit gather");
+  // One launch: A side the P + 1 weight-side sources in order, B side the
+  // gather outputs 1 .. P (im2col(A_p)).
+  KernelTimer timer("limb_planes", s);
+  PlanesLaunch pl;
+  memset(&pl, 0, sizeof(pl));
+  pl.cg = cg;
+  for (int j = 0; j <= P; ++j)
+    pl.ja.j[j] = PlaneJob{asrc[j], nullptr,
+                          reinterpret_cast<__nv_bfloat16*>(w + (size_t)j * a_bytes)};
+  for (int p = 0; p < P; ++p)
+    pl.jb.j[1 + p] = PlaneJob{nullptr, nullptr,
+                              reinterpret_cast<__nv_bfloat16*>(w + (size_t)(P + 1) * a_bytes +
+                                                               (size_t)p * b_bytes)};
+  pl.M = M;
+  pl.N = N;
+  pl.K = K;
+  pl.Kp = K1p;
+  pl.na = P + 1;
+  pl.a_blk = (int)std::min<i64>(ceil_div(M * (K1p / 8), 256), 148 * 4);
+  pl.nb = P;
+  pl.z0 = 1;
+  pl.bx = (int)ceil_div(K1p / KS, 8);
+  pl.by = (int)ceil_div(N, 16);
+  const i64 blocks = (i64)pl.na * pl.a_blk + (i64)P * pl.bx * pl.by;
+  if (blocks > 0x7FFFFFFFll) return fail(MPC_EUNSUPPORTED, "plane pass grid too large");
+  limb_planes<true><<<(unsigned)blocks, 256, 0, s>>>(pl);
+  return check_launch("limb_planes");
+}
+
 int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream_t s) {
   GemmArgs g = g_in;
   if (g.splits < 1) g.splits = 1;
@@ -1482,8 +1528,11 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     return fail(MPC_EINVAL, "bad split configuration");
   if (!limb_supported(g.M, g.N, g.K)) return fail(MPC_EUNSUPPORTED, "shape outside limb engine");
   if (int rc = get_encoder()) return rc;
-  const int npairs = g.jobs[0].A2 ? 2 : 1;
-  for (int j = 1; j < g.njobs; ++j)
+  const bool prep = g.prep != nullptr;
+  if (prep && g.gather == nullptr)
+    return fail(MPC_EINVAL, "limb engine: prepared planes need the convolution gather");
+  const int npairs = (prep || g.jobs[0].A2) ? 2 : 1;
+  for (int j = 1; j < g.njobs && !prep; ++j)
     if ((g.jobs[j].A2 != nullptr) != (npairs == 2))
       return fail(MPC_EINVAL, "limb engine: jobs mix one- and two-pair products");
   const i64 K1p = pair_k(g.K);
@@ -1504,7 +1553,16 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   const size_t a_bytes = al256((size_t)8 * g.M * K1p * 2), b_bytes = al256((size_t)8 * g.N * K1p * 2);
   PlaneJobs ja = {}, jbv = {};
   int na = 0, nb = 0;
-  for (int pr = 0; pr < npairs; ++pr) {
+  // Prepared planes (limb_conv_prepare): G, B_1 .. B_{P-1}, F, then im2col(A_p).
+  const char* pp = static_cast<const char*>(g.prep);
+  if (prep) {
+    for (int j = 0; j < g.njobs; ++j) {
+      if (int rc = encode_planes(&prm.tmA[0][j], pp + (size_t)j * a_bytes, g.M, K1p, BM)) return rc;
+      if (int rc = encode_planes(&prm.tmA[1][j], pp + (size_t)g.njobs * a_bytes, g.M, K1p, BM))
+        return rc;
+    }
+  }
+  for (int pr = 0; pr < npairs && !prep; ++pr) {
     for (int j = 0; j < g.njobs; ++j) {
       const u64* src = pr ? g.jobs[j].A2 : g.jobs[j].A1;
       int hit = -1;
@@ -1520,15 +1578,19 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   }
   if (g.gather) {
     // pair 1: the opened gather, shared; pair 2 (two-pair products): one per job
-    nb = npairs == 2 ? 1 + g.njobs : 1;
+    nb = (npairs == 2 && !prep) ? 1 + g.njobs : 1;
     for (int z = 0; z < nb; ++z) {
       jbv.j[z] = PlaneJob{nullptr, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
       w += b_bytes;
     }
     for (int j = 0; j < g.njobs; ++j) {
       if (int rc = encode_planes(&prm.tmB[0][j], jbv.j[0].out, g.N, K1p, BN)) return rc;
-      if (npairs == 2)
+      if (prep) {
+        const char* bj = pp + (size_t)(g.njobs + 1) * a_bytes + (size_t)j * b_bytes;
+        if (int rc = encode_planes(&prm.tmB[1][j], bj, g.N, K1p, BN)) return rc;
+      } else if (npairs == 2) {
         if (int rc = encode_planes(&prm.tmB[1][j], jbv.j[1 + j].out, g.N, K1p, BN)) return rc;
+      }
     }
   } else {
     for (int pr = 0; pr < npairs; ++pr) {

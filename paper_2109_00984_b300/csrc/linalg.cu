@@ -371,19 +371,21 @@ namespace {
 
 // The Beaver convolution; with `deferred`, a split-K job set leaves its partial
 // sums for the caller (the job set as launched is copied there).
+// prep (limb engine only): the planes limb_conv_prepare cut from W and B ahead
+// of the call; W and B are then not read.
 int beaver_conv2d_impl(int P, const mpc_conv_desc* d, const uint64_t* X, const uint64_t* W,
                        const uint64_t* A, const uint64_t* B, const uint64_t* C, uint64_t* Z,
                        int algo, int trunc_bits, void* ws, size_t ws_bytes, void* stream,
-                       GemmArgs* deferred) {
+                       GemmArgs* deferred, const void* prep = nullptr) {
   MPC_CHECK_PARTIES(P);
   if (int rc = check_algo(algo)) return rc;
   i64 ho, wo;
   if (int rc = validate_conv(d, &ho, &wo)) return rc;
   MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
-  MPC_REQUIRE(X && W && A && B && C && Z, "null pointer");
+  MPC_REQUIRE(X && A && C && Z && (prep || (W && B)), "null pointer");
   const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
   const i64 nx = d->batch * d->c_in * d->h * d->w;
-  algo = resolve_algo(algo, M, N, K);
+  algo = prep ? MPC_ALGO_LIMB : resolve_algo(algo, M, N, K);
   if (algo == MPC_ALGO_LIMB && !limb_supported(M, N, K))
     return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
   const size_t need = conv_ws(P, *d, ho, wo, algo);
@@ -421,9 +423,12 @@ int beaver_conv2d_impl(int P, const mpc_conv_desc* d, const uint64_t* X, const u
                                  Acol[p], s))
         return rc;
   }
-  MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
-  if (int rc = check_launch("open F")) return rc;
+  if (!prep) {
+    MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
+    if (int rc = check_launch("open F")) return rc;
+  }
   GemmArgs g{};
+  g.prep = prep;
   g.M = M;
   g.N = N;
   g.K = K;
@@ -433,7 +438,7 @@ int beaver_conv2d_impl(int P, const mpc_conv_desc* d, const uint64_t* X, const u
   g.gather = gather ? &cg : nullptr;
   g.defer_reduce = deferred != nullptr;
   for (int p = 0; p < P; ++p) {
-    g.jobs[p].A1 = p == 0 ? G : (const u64*)B + (i64)p * M * K;
+    g.jobs[p].A1 = p == 0 ? G : (prep ? nullptr : (const u64*)B + (i64)p * M * K);
     g.jobs[p].B1 = Ecol;
     g.jobs[p].A2 = F;
     g.jobs[p].B2 = Acol[p];
@@ -441,9 +446,10 @@ int beaver_conv2d_impl(int P, const mpc_conv_desc* d, const uint64_t* X, const u
     g.jobs[p].Z = (u64*)Z + (i64)p * M * N;
   }
   int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, deferred);
+  // With prepared planes F was opened (and counted) by the prepare call.
   if (rc == MPC_OK)
-    stats_add(1, 8ull * (uint64_t)(nx + M * K), 0, (uint64_t)P * (nx + M * K + M * N),
-              (uint64_t)P * 2ull * M * N * K);
+    stats_add(1, 8ull * (uint64_t)(nx + (prep ? 0 : M * K)), 0,
+              (uint64_t)P * (nx + M * K + M * N), (uint64_t)P * 2ull * M * N * K);
   return rc;
 }
 
@@ -469,6 +475,80 @@ int mpc_beaver_conv2d_relu(int P, const mpc_conv_desc* d, const uint64_t* X, con
   used.njobs = 0;
   if (int rc = beaver_conv2d_impl(P, d, X, W, A, B, C, Y, algo, trunc_bits, ws, ws_bytes, stream,
                                   &used))
+    return rc;
+  if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
+  return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
+}
+
+size_t mpc_conv2d_prep_size(int P, const mpc_conv_desc* d) {
+  i64 ho, wo;
+  if (P < 1 || P > MPC_MAX_PARTIES || validate_conv(d, &ho, &wo) != MPC_OK) return 0;
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  if (!limb_supported(M, N, K)) return 0;
+  // the planes, then F and G (the opened weight difference, scratch)
+  return limb_conv_prep_bytes(P, M, N, K) + 2 * align256(words(M * K));
+}
+
+int mpc_beaver_conv2d_prepare(int P, const mpc_conv_desc* d, const uint64_t* W, const uint64_t* A,
+                              const uint64_t* B, void* prep, size_t prep_bytes, void* stream) {
+  MPC_CHECK_PARTIES(P);
+  i64 ho, wo;
+  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  if (M * N * K == 0) return MPC_OK;
+  MPC_REQUIRE(W && A && B && prep, "null pointer");
+  if (!limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
+  const size_t planes = limb_conv_prep_bytes(P, M, N, K);
+  const size_t need = planes + 2 * align256(words(M * K));
+  if (prep_bytes < need) return fail(MPC_ENOMEM, "prep buffer %zu bytes, need %zu", prep_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  u64* F = reinterpret_cast<u64*>(static_cast<char*>(prep) + planes);
+  u64* G = F + align256(words(M * K)) / sizeof(u64);
+  MPC_DISPATCH_P(P, launch_open, M * K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
+  if (int rc = check_launch("open F")) return rc;
+  const u64* asrc[MPC_MAX_PARTIES + 1];
+  asrc[0] = G;
+  for (int p = 1; p < P; ++p) asrc[p] = (const u64*)B + (i64)p * M * K;
+  asrc[P] = F;
+  ConvGather cg{};
+  cg.d = *d;
+  cg.ho = ho;
+  cg.wo = wo;
+  cg.stride1 = d->batch * d->c_in * d->h * d->w;
+  cg.n1 = P;
+  for (int p = 0; p < P; ++p) cg.src2[p] = (const u64*)A + p * cg.stride1;
+  const int rc = limb_conv_prepare(P, cg, M, N, K, asrc, prep, s);
+  if (rc == MPC_OK) stats_add(1, 8ull * (uint64_t)(M * K), 0, 0, 0);
+  return rc;
+}
+
+int mpc_beaver_conv2d_prepared(int P, const mpc_conv_desc* d, const uint64_t* X,
+                               const uint64_t* A, const uint64_t* C, const void* prep,
+                               size_t prep_bytes, uint64_t* Z, int trunc_bits, void* ws,
+                               size_t ws_bytes, void* stream) {
+  const size_t need = mpc_conv2d_prep_size(P, d);
+  MPC_REQUIRE(prep != nullptr, "null prep buffer");
+  if (need == 0) return fail(MPC_EUNSUPPORTED, "no prepared planes for this shape or party count");
+  if (prep_bytes < need) return fail(MPC_ENOMEM, "prep buffer %zu bytes, need %zu", prep_bytes, need);
+  return beaver_conv2d_impl(P, d, X, nullptr, A, nullptr, C, Z, MPC_ALGO_LIMB, trunc_bits, ws,
+                            ws_bytes, stream, nullptr, prep);
+}
+
+int mpc_beaver_conv2d_relu_prepared(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                    const uint64_t* A, const uint64_t* C, const void* prep,
+                                    size_t prep_bytes, uint64_t* Y, int trunc_bits, uint64_t seed,
+                                    uint64_t relu_op, void* ws, size_t ws_bytes, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "convolution + fused ReLU supports P = 2 (got %d)", P);
+  const size_t need = mpc_conv2d_prep_size(P, d);
+  MPC_REQUIRE(prep != nullptr, "null prep buffer");
+  if (need == 0) return fail(MPC_EUNSUPPORTED, "no prepared planes for this shape");
+  if (prep_bytes < need) return fail(MPC_ENOMEM, "prep buffer %zu bytes, need %zu", prep_bytes, need);
+  GemmArgs used{};
+  used.njobs = 0;
+  if (int rc = beaver_conv2d_impl(P, d, X, nullptr, A, nullptr, C, Y, MPC_ALGO_LIMB, trunc_bits,
+                                  ws, ws_bytes, stream, &used, prep))
     return rc;
   if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
   return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));

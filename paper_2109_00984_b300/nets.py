@@ -17,7 +17,11 @@ The dealer's work depends only on shapes and op ids, never on the data, so
 with overlap_dealer (the default) every layer's convolution triple is dealt on
 a second stream that runs ahead of the online phase; the online convolution of
 layer l waits on an event recorded after layer l's triple.  Each stream has its
-own workspace.
+own workspace.  With the limb engine the dealer stream also runs the
+convolution's input-independent half right after the triple
+(beaver_conv2d_prepare: opening F = W - B, the weight-side digit planes and
+those of im2col(A_p)); the online phase runs beaver_conv2d_relu_prepared on them
+(bit-identical to beaver_conv2d_relu).
 """
 import torch
 
@@ -26,7 +30,8 @@ from . import api
 
 class PrivateConv1dStack:
     def __init__(self, weights, strides, pads, frames, batch=1, algo=api.PLAIN, frac_bits=16,
-                 weight_ops=None, seed=1, device="cuda", fused_relu=True, overlap_dealer=True):
+                 weight_ops=None, seed=1, device="cuda", fused_relu=True, overlap_dealer=True,
+                 prepare_weights=False):
         self.P = 2
         self.fused_relu = fused_relu
         self.overlap_dealer = overlap_dealer
@@ -48,6 +53,7 @@ class PrivateConv1dStack:
         self.out_len = L
         self.in_shape = (batch, weights[0].shape[1], frames)
         self._alloc()
+        self.enable_prepared(prepare_weights)
 
     def _alloc(self):
         P, dev = self.P, self.device
@@ -64,6 +70,9 @@ class PrivateConv1dStack:
             )
             ws_bytes = max(ws_bytes, api.conv2d_workspace_size(P, d, self.algo),
                            api.conv2d_triple_workspace_size(P, d, self.algo))
+            if self.fused_relu and self.algo != api.PLAIN:
+                # the prepared convolution always runs on the limb engine
+                ws_bytes = max(ws_bytes, api.conv2d_workspace_size(P, d, api.LIMB))
             if not self.fused_relu:
                 b.update(T=torch.empty((api.KS_GATES, 3, P, n), dtype=torch.int64, device=dev),
                          ra=torch.empty((P, n), dtype=torch.int64, device=dev),
@@ -78,6 +87,8 @@ class PrivateConv1dStack:
             C=torch.empty((P, d.batch, d.c_out) + tuple(api.conv_out_hw(d)), dtype=torch.int64,
                           device=dev)) for d in self.descs] for _ in range(2)]
         self.ready = [[None] * len(self.descs) for _ in range(2)]
+        self.prepared = False
+        self.prep = None
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         self.dealer_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         # The online phase is the critical path: it runs on a high-priority stream,
@@ -88,6 +99,21 @@ class PrivateConv1dStack:
             else None
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
                                     dtype=torch.float64, device=dev)
+
+    def enable_prepared(self, on=True):
+        """With `on` (limb engine, fused ReLU) the input-independent half of each
+        convolution -- opening F = W - B, the weight-side digit planes and those
+        of im2col(A_p) -- is done by the dealer right after the layer's triple,
+        into a prepared-plane buffer per layer and triple slot, and the online
+        phase only cuts im2col(E) before its GEMM.  That shortens the online
+        phase (its latency); with the dealer overlapped the total work is the
+        same, so it does not raise throughput.  Takes effect from the next deal."""
+        ok = on and self.fused_relu and self.algo != api.PLAIN and all(
+            api.conv2d_prep_size(self.P, d) > 0 for d in self.descs)
+        if ok and self.prep is None:
+            self.prep = [[torch.empty(api.conv2d_prep_size(self.P, d), dtype=torch.uint8,
+                                      device=self.device) for d in self.descs] for _ in range(2)]
+        self.prepared = ok
 
     def deal(self, schedule, slot=0, join=False):
         """Enqueue the dealer's convolution triples of every layer for `schedule`
@@ -106,6 +132,9 @@ class PrivateConv1dStack:
                 api.ttp_conv2d_triple(self.P, d, seed, schedule["layers"][l]["conv"], self.algo,
                                       out=(t["A"], t["B"], t["C"]),
                                       ws=self.dealer_ws if ds is not main else self.ws)
+                if self.prepared:
+                    api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], d,
+                                              out=self.prep[slot][l])
                 if ds is not main:
                     ev = torch.cuda.Event()
                     ev.record(ds)
@@ -164,6 +193,9 @@ class PrivateConv1dStack:
             if deal:
                 api.ttp_conv2d_triple(self.P, d, seed, ops["conv"], self.algo,
                                       out=(t["A"], t["B"], t["C"]), ws=self.ws)
+                if self.prepared:
+                    api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], d,
+                                              out=self.prep[slot][l])
             elif wait_dealer and self.ready[slot][l] is not None:
                 main.wait_event(self.ready[slot][l])
             n = b["n"]
@@ -172,9 +204,14 @@ class PrivateConv1dStack:
                                                                  ops["and"] + 3)
                 # convolution + truncation + ReLU: the ReLU kernel reduces the
                 # GEMM's split-K partial sums itself
-                api.beaver_conv2d_relu(X, self.W[l], t["A"], t["B"], t["C"], d, seed, ops["and"],
-                                       self.algo, trunc_bits=self.frac_bits, out=b["Y"],
-                                       ws=self.ws)
+                if self.prepared:
+                    api.beaver_conv2d_relu_prepared(X, t["A"], t["C"], self.prep[slot][l], d,
+                                                    seed, ops["and"], trunc_bits=self.frac_bits,
+                                                    out=b["Y"], ws=self.ws)
+                else:
+                    api.beaver_conv2d_relu(X, self.W[l], t["A"], t["B"], t["C"], d, seed,
+                                           ops["and"], self.algo, trunc_bits=self.frac_bits,
+                                           out=b["Y"], ws=self.ws)
             else:
                 api.beaver_conv2d(X, self.W[l], t["A"], t["B"], t["C"], d, self.algo,
                                   trunc_bits=self.frac_bits, out=b["Z"], ws=self.ws)

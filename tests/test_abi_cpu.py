@@ -148,3 +148,20 @@ def test_noalloc_size_refused_before_any_device_work(lib):
 def test_wait_timeout_limit_validated(lib):
     assert lib.mpc_test_wait_timeout(10, NULL) == E["EINVAL"]
     assert lib.mpc_test_wait_timeout(2_000_000_000, NULL) == E["EINVAL"]
+
+
+def test_prepared_conv_validation(lib):
+    from paper_2109_00984_b300 import _lib
+    d = _lib.ConvDesc(1, 16, 1, 64, 32, 1, 7, 1, 1, 0, 3)
+    need = lib.mpc_conv2d_prep_size(2, ctypes.byref(d))
+    K1p = 16 * 7
+    assert need >= 16 * K1p * (3 * 32 + 2 * 64)
+    assert lib.mpc_conv2d_prep_size(0, ctypes.byref(d)) == 0
+    assert lib.mpc_beaver_conv2d_prepare(2, ctypes.byref(d), FAKE, FAKE, FAKE, FAKE, need - 1,
+                                         NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_conv2d_prepared(2, ctypes.byref(d), FAKE, FAKE, FAKE, FAKE, need - 1,
+                                          FAKE, 16, FAKE, 1 << 20, NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_conv2d_relu_prepared(3, ctypes.byref(d), FAKE, FAKE, FAKE, FAKE, need,
+                                               FAKE, 16, 1, 1, FAKE, 1 << 20, NULL) == E["EUNSUPPORTED"]
+    assert lib.mpc_beaver_conv2d_prepared(2, ctypes.byref(d), FAKE, FAKE, FAKE, NULL, need,
+                                          FAKE, 16, FAKE, 1 << 20, NULL) == E["EINVAL"]

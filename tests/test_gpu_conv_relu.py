@@ -72,3 +72,49 @@ def test_conv2d_relu_rejects_other_party_counts(mpc):
     rc = lib.mpc_beaver_conv2d_relu(3, ctypes.byref(d), fake, fake, fake, fake, fake, fake, 0, 16,
                                     1, 1, fake, 1 << 20, None)
     assert rc == -6
+
+
+@pytest.mark.parametrize("geom", GEOMS)
+def test_prepared_conv2d_relu_matches_oracle(mpc, geom, rng):
+    """The convolution split into its input-independent half (prepare: F opened,
+    weight-side and im2col(A_p) digit planes) and the online half gives the
+    oracle's words, with the ReLU and without it; the prepare call reads no X
+    (done before X exists) and the online calls read neither W nor B."""
+    b, ci, h, w, co, kh, kw, st, ph, pw = geom
+    P = 2
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 91, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    n = Z[0].size
+    op = 500
+    T = dealer.and_triples(P, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(P, n, SEED, op + 1)
+    mt = dealer.mul_triple(P, n, SEED, op + 2)
+    ref = binary.private_relu(Z.reshape(P, n), T, ra, rb, mt, SEED, op + 3).reshape(Z.shape)
+
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    dA = dev(A)
+    prep = mpc.beaver_conv2d_prepare(dev(W), dA, dev(B), d)
+    Zp = mpc.beaver_conv2d_prepared(dev(X), dA, dev(C), prep, d, trunc_bits=16)
+    Y = mpc.beaver_conv2d_relu_prepared(dev(X), dA, dev(C), prep, d, SEED, op, trunc_bits=16)
+    mpc.sync_status()
+    assert np.array_equal(host(Zp), Z)
+    assert np.array_equal(host(Y), ref)
+
+
+@pytest.mark.parametrize("P", [3, 8])
+def test_prepared_conv2d_more_parties(mpc, P, rng):
+    b, ci, h, w, co, kh, kw, st, ph, pw = GEOMS[1]
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 92, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    dA = dev(A)
+    prep = mpc.beaver_conv2d_prepare(dev(W), dA, dev(B), d)
+    Zp = mpc.beaver_conv2d_prepared(dev(X), dA, dev(C), prep, d, trunc_bits=16)
+    mpc.sync_status()
+    assert np.array_equal(host(Zp), Z)

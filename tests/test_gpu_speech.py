@@ -112,15 +112,19 @@ def test_full_speech_stack_graph_replay_bit_exact(mpc, full_oracle):
     assert nmse < 4e-4
 
 
-def test_small_stack_pipelined_bit_exact(mpc):
+@pytest.mark.parametrize("prepared", [False, True])
+def test_small_stack_pipelined_bit_exact(mpc, prepared):
     """Software-pipelined steps (online phase of batch i on the triples dealt
     during step i - 1), as graph replays and eagerly: every output equals the
-    oracle's forward for its own schedule."""
+    oracle's forward for its own schedule.  prepared: the dealer also runs each
+    convolution's input-independent half (beaver_conv2d_prepare)."""
     from paper_2109_00984_b300.nets import PrivateConv1dStack
     x, ws, strides, pads = synth.speech_small()
     scheds = [synth.speech_schedule(len(ws), step=s) for s in (11, 12, 13, 14)]
     net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=mpc.AUTO,
-                             weight_ops=scheds[0]["weight_op"], seed=scheds[0]["seed"])
+                             weight_ops=scheds[0]["weight_op"], seed=scheds[0]["seed"],
+                             prepare_weights=prepared)
+    assert net.prepared == prepared
     xd = dev_f64(x)
     refs = [_oracle(x, ws, strides, pads, s) for s in scheds[:3]]
     graphs = net.capture_pipelined(xd, scheds[:3], scheds[1:])
@@ -159,3 +163,20 @@ def test_small_stack_pipelined_two_input_buffers(mpc):
         torch.cuda.synchronize()
         assert np.array_equal(host(net.bufs[-1]["Y"]).reshape(ref_shares.shape), ref_shares)
         assert np.array_equal(out.cpu().numpy().reshape(ref_real.shape), ref_real)
+
+
+@pytest.mark.slow
+def test_full_speech_stack_prepared_bit_exact(mpc, full_oracle):
+    """The full stack with the convolutions' input-independent half on the
+    dealer (the online-latency schedule) gives the oracle's shares."""
+    from paper_2109_00984_b300.nets import PrivateConv1dStack
+    x, ws, strides, pads = synth.speech_stack()
+    sched = synth.speech_schedule(len(ws))
+    net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=mpc.AUTO,
+                             weight_ops=sched["weight_op"], seed=sched["seed"],
+                             prepare_weights=True)
+    assert net.prepared
+    Y = net.forward(dev_f64(x), sched)
+    torch.cuda.synchronize()
+    ref_shares, plain = full_oracle
+    assert np.array_equal(host(Y).reshape(ref_shares.shape), ref_shares)
