@@ -463,7 +463,6 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const int steps = t_end - t_begin;
 
   if (warp < kIssuers) {
     // The MMA and producer warpgroups hand registers to the drain warpgroups:
@@ -1116,22 +1115,10 @@ struct PlaneJobs {
   PlaneJob j[2 * MPC_MAX_PARTIES];
 };
 
-// Element sources of the plane pass.  Direct: the word at index i.  Opened
-// (fused Beaver opening, App. D.1.1): sum_p (X[p][i] - S[p][i]) over the P
-// parties' shares, plus add[i] when given (G = B_0 + F).
+// Element source of the per-GEMM plane pass: the word at index i.
 struct DirectSrc {
   const u64* X;
   __device__ __forceinline__ u64 operator()(i64 i) const { return X[i]; }
-};
-struct OpenedSrc {
-  const u64 *X, *S, *add;
-  i64 pstride;
-  int P;
-  __device__ __forceinline__ u64 operator()(i64 i) const {
-    u64 acc = add ? add[i] : 0ull;
-    for (int p = 0; p < P; ++p) acc += X[p * pstride + i] - S[p * pstride + i];
-    return acc;
-  }
 };
 
 // A side: the source is [M][K] row-major.  Block `blk` of `nblk` strides over
@@ -1157,12 +1144,10 @@ __device__ __forceinline__ void planes_a_part(const Src& src, __nv_bfloat16* out
 // below: lane l of warp w owns column n = 16 by + l / 2 and the 8 consecutive
 // k of half l % 2 of sub-step t = 8 bx + w, reads them (16 consecutive n per
 // warp and k: whole 128-byte lines) and writes its digits straight into the
-// planes, one 16-byte store per plane.  With add (dual), the planes of v + add
-// go to out2 as well (F and G = B_0 + F of a Beaver product).
+// planes, one 16-byte store per plane.
 template <class Src>
-__device__ __forceinline__ void planes_b_kmajor(const Src& src, const u64* add,
-                                                __nv_bfloat16* out, __nv_bfloat16* out2, i64 N,
-                                                i64 K, i64 Kp, int bx, int by) {
+__device__ __forceinline__ void planes_b_kmajor(const Src& src, __nv_bfloat16* out, i64 N, i64 K,
+                                                i64 Kp, int bx, int by) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const i64 t = (i64)bx * 8 + w;
   const i64 n = (i64)by * 16 + (l >> 1);
@@ -1172,12 +1157,6 @@ __device__ __forceinline__ void planes_b_kmajor(const Src& src, const u64* add,
 #pragma unroll
   for (int e = 0; e < 8; ++e) v[e] = k0 + e < K ? src((k0 + e) * N + n) : 0ull;
   write_planes(v, out, n, Kp, k0);
-  if (out2) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (k0 + e < K) v[e] += add[(k0 + e) * N + n];
-    write_planes(v, out2, n, Kp, k0);
-  }
 }
 
 // B side of a convolution, gathered straight from the data (implicit im2col),
@@ -1269,16 +1248,14 @@ __global__ void __launch_bounds__(256) limb_planes(const __grid_constant__ Plane
   if (GATHER)
     planes_b_conv_kmajor(pl.cg, pl.jb, (int)pl.N, (int)pl.K, (int)pl.Kp, bx, by, z);
   else
-    planes_b_kmajor(DirectSrc{pl.jb.j[z].X1}, nullptr, pl.jb.j[z].out, nullptr, pl.N, pl.K, pl.Kp,
+    planes_b_kmajor(DirectSrc{pl.jb.j[z].X1}, pl.jb.j[z].out, pl.N, pl.K, pl.Kp,
                     bx, by);
 }
 
-// The digit planes of many products in one launch: a task is one operand
-// source (A side [rows][K] or B side [K][rows], row-major u64) with its plane
-// buffer; block b belongs to the last task whose block_base <= b.  With
-// nparty > 0 the source is opened on the fly: element i is
-// sum_p (src[p][i] - sub[p][i]) (+ add[i]), party p at p * pstride.  A B-side
-// task with out2 also writes the planes of that element plus add2[i] to out2.
+// The digit planes of many products in one launch (limb_planes_grouped): a
+// task is one side of one product, block b belongs to the last task whose
+// block_base <= b.
+//
 // A side of a Beaver product, from one read of X and A: the opened
 // E = sum_p (X_p - A_p) and every party's A_p, each cut into digit planes
 // ([M][K] row-major sources, parties pstride words apart); E's planes go to
