@@ -38,6 +38,10 @@ L2_FLUSH_BYTES = 256 << 20
 # for two parties), from an ncu capture of dram__bytes_read.sum +
 # dram__bytes_write.sum on the current kernel.
 LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 59.3e6
+# ncu sm__pipe_tensor_cycles_active (% of elapsed cycles) of the same kernel in
+# one capture each: an online speech-layer launch, and the 4096^3 ring GEMM.
+LIMB_GEMM_TENSOR_ACTIVE_SPEECH = 64.4
+LIMB_GEMM_TENSOR_ACTIVE_4096 = 80.7
 REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
 
 
@@ -449,6 +453,9 @@ def run_ours(args):
                 "traffic": LIMB_GEMM_DRAM_BYTES_PER_LAUNCH,
                 "traffic_note": "bytes per launch, mean of the 14 limb GEMM launches of one "
                                 "step (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
+                "ncu_tensor_active_pct": LIMB_GEMM_TENSOR_ACTIVE_SPEECH,
+                "ncu_tensor_active_note": "sm__pipe_tensor_cycles_active of an online "
+                                          "speech-layer launch, one ncu capture (serialised)",
                 "peak_source": peak_src + " (bf16 burst)",
                 "launches_per_step": launches / args.steps,
                 "busy_ms_per_step": kms / args.steps,
@@ -580,6 +587,8 @@ def measure_ring_gemm(n, algo, dev, reps, flush, bf16_burst):
         rec["tensor_tflops"] = 72 * n ** 3 / (k_ms / 1e3) / 1e12   # 36 digit-pair MMAs per MAC
         rec["tensor_frac"] = rec["tensor_tflops"] / bf16_burst
         rec["tensor_frac_peak"] = "bf16 burst (the kernel is timed alone)"
+        if n == 4096:
+            rec["ncu_tensor_active_pct"] = LIMB_GEMM_TENSOR_ACTIVE_4096
     else:
         rec["alu_frac"] = rec["ring_tops"] / PLAIN_PEAK_TOPS
         rec["alu_peak_ring_tops"] = PLAIN_PEAK_TOPS
