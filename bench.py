@@ -598,7 +598,7 @@ def measure_ring_gemm(n, algo, dev, reps, flush, bf16_burst):
 
 
 def measure_beaver3(n, algo, dev, reps, flush):
-    """The three-party Beaver online step on an n x n x n product (SURVEY config 3 (ii)):
+    """The three-party Beaver online step on an n x n x n product (the GEMM sweep's 3-party case):
     opening of E and F, then per party one ring GEMM over the K-concatenated pairs
     [E | A_p] [B_p (+ F) ; F] (K' = 2n), plus C_p and the truncation; triples dealt
     beforehand.  Ring ops = 2 x 3 parties x n^2 x 2n."""
