@@ -76,6 +76,48 @@ __global__ void __launch_bounds__(kThreads) fill_sum_kernel(int P, i64 n, u64 se
   }
 }
 
+// The two-party dealer fill with one Philox block per lane: lanes 2j and 2j + 1
+// of a warp produce parties 0 and 1 of one 4-word group, and the pair's sum
+// is formed with one shuffle.  Twice the threads of fill_sum_kernel's P = 2
+// path for the same blocks: a fill of a few hundred thousand words otherwise
+// runs a few warps per SM, too few to hide the Philox rounds' latency.  The
+// loop runs over whole warps so that every lane takes part in the shuffles.
+__global__ void __launch_bounds__(kThreads) fill_sum2_kernel(i64 n, u64 seed, u64 op_id,
+                                                             unsigned role, u64* __restrict__ Out,
+                                                             u64* __restrict__ sum) {
+  const i64 nblk = ceil_div(n, 4);
+  const int lane = threadIdx.x & 31, p = lane & 1;
+  const i64 wstride = (i64)gridDim.x * blockDim.x;
+  for (i64 wb = (blockIdx.x * (i64)blockDim.x + threadIdx.x) - lane; wb < 2 * nblk;
+       wb += wstride) {
+    const i64 t = (wb + lane) >> 1;
+    const bool valid = t < nblk;
+    const u64x4 r = prg_block(seed, op_id, stream_word2(role, 0, p), valid ? t : 0);
+    const i64 i0 = 4 * t;
+    if (valid) store4(Out + (i64)p * n, i0, n, as_quad(r));
+    if (sum) {
+      Quad q;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) q.v[j] = r.v[j] + __shfl_xor_sync(0xffffffffu, r.v[j], 1);
+      if (valid && p == 0) store4(sum, i0, n, q);
+    }
+  }
+}
+
+// Launches the dealer fill (two parties: fill_sum2_kernel).
+int launch_fill_sum(int P, i64 n, u64 seed, u64 op_id, unsigned role, u64* Out, u64* sum,
+                    cudaStream_t s) {
+  if (n <= 0) return MPC_OK;
+  if (P == 2)
+    fill_sum2_kernel<<<grid_for(2 * ceil_div(n, 4), kThreads), kThreads, 0, s>>>(n, seed, op_id,
+                                                                                 role, Out, sum);
+  else
+    fill_sum_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(P, n, seed, op_id,
+                                                                             role, Out, sum);
+  return check_launch("dealer fill");
+}
+
+
 // Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1 and C[P-1] =
 // c - sum_{p<P-1} C[p].  c is C[P-1] on entry, or, when the product's GEMM was
 // split along K (part != null), the sum of its `splits` partial sums
@@ -609,16 +651,8 @@ int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed,
   Carve cv(ws);
   u64* a = cv.take(M * K);
   u64* b = cv.take(K * N);
-  if (M * K > 0) {
-    fill_sum_kernel<<<grid_for(ceil_div(M * K, 4), kThreads), kThreads, 0, s>>>(
-        P, M * K, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a);
-    if (int rc = check_launch("fill A")) return rc;
-  }
-  if (K * N > 0) {
-    fill_sum_kernel<<<grid_for(ceil_div(K * N, 4), kThreads), kThreads, 0, s>>>(
-        P, K * N, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b);
-    if (int rc = check_launch("fill B")) return rc;
-  }
+  if (int rc = launch_fill_sum(P, M * K, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a, s)) return rc;
+  if (int rc = launch_fill_sum(P, K * N, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b, s)) return rc;
   if (M * N == 0) return MPC_OK;
   u64* Clast = (u64*)C + (i64)(P - 1) * M * N;
   GemmArgs g{};
@@ -662,12 +696,8 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   u64* a = cv.take(nx);
   u64* acol = gather ? nullptr : cv.take(K * N);
   u64* b = cv.take(M * K);
-  fill_sum_kernel<<<grid_for(ceil_div(nx, 4), kThreads), kThreads, 0, s>>>(
-      P, nx, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a);
-  if (int rc = check_launch("fill A")) return rc;
-  fill_sum_kernel<<<grid_for(ceil_div(M * K, 4), kThreads), kThreads, 0, s>>>(
-      P, M * K, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b);
-  if (int rc = check_launch("fill B")) return rc;
+  if (int rc = launch_fill_sum(P, nx, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a, s)) return rc;
+  if (int rc = launch_fill_sum(P, M * K, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b, s)) return rc;
   ConvGather cg{};
   if (gather) {
     cg.d = *d;
