@@ -114,13 +114,17 @@ def test_matmul_triple_limb(mpc, P):
     assert np.array_equal(host(C), rC)
 
 
+@pytest.mark.parametrize("P", [2, 3])
 @pytest.mark.parametrize("geom", [
     dict(batch=2, c_in=3, h=9, w=7, c_out=5, k=3, stride=2, pad=1),
     dict(batch=1, c_in=16, h=12, w=12, c_out=130, k=3, stride=1, pad=1),
+    # batch 2, stride 2, padding, a non-square input and ragged tiles
+    dict(batch=2, c_in=32, h=9, w=11, c_out=24, k=3, stride=2, pad=1),
+    # one tap, stride 2 (a ResNet downsampling shortcut)
+    dict(batch=2, c_in=16, h=7, w=9, c_out=24, k=1, stride=2, pad=0),
 ])
-def test_beaver_conv2d_limb(mpc, geom, rng):
+def test_beaver_conv2d_limb(mpc, geom, P, rng):
     g = geom
-    P = 2
     d = mpc.conv_desc(g["batch"], g["c_in"], g["h"], g["w"], g["c_out"], g["k"], g["k"],
                       g["stride"], g["stride"], g["pad"], g["pad"])
     xs = (g["batch"], g["c_in"], g["h"], g["w"])
