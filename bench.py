@@ -164,6 +164,66 @@ def _oracle_sample_seconds(step):
 
 ORACLE_MAX_PROCS = 32
 
+# Oracle samples of the other workloads, bounded (a few seconds each).
+ORACLE_GEMM_N = 1024          # ring GEMM n^3: numpy uint64 matmul, not BLAS
+ORACLE_RESNET_HW = (56, 112)  # one image at two resolutions, extrapolated to 224
+
+
+def _oracle_gemm_rows(args):
+    """Rows [r0, r1) of the n^3 ring GEMM through the oracle; compute seconds."""
+    from oracle import ring
+    n, r0, r1 = args
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 2 ** 64, (n, n), dtype=np.uint64)
+    b = rng.integers(0, 2 ** 64, (n, n), dtype=np.uint64)
+    t = time.perf_counter()
+    ring.matmul(a[r0:r1], b)
+    return time.perf_counter() - t
+
+
+def oracle_gemm_measure(n=ORACLE_GEMM_N, all_cores=True):
+    """The oracle's ring GEMM at n^3 on one core and as row blocks over all cores."""
+    dt = _oracle_gemm_rows((n, 0, n))
+    out = {"value": 2 * n ** 3 / dt / 1e12, "unit": "ring TOPS", "cores": 1, "kind": "oracle",
+           "sample": f"M = N = K = {n} ({dt:.1f} s; numpy uint64 matmul, single-threaded); "
+                     f"at 4096^3 / 8192^3 this rate gives {64 * dt:.0f} / {512 * dt:.0f} s "
+                     f"(extrapolated by n^3; the per-MAC rate falls as n grows)",
+           "extrapolated_s": {"4096": 64 * dt, "8192": 512 * dt}}
+    if all_cores:
+        import multiprocessing
+        procs = max(1, min(os.cpu_count() or 1, ORACLE_MAX_PROCS))
+        bounds = [(n, i * n // procs, (i + 1) * n // procs) for i in range(procs)]
+        with multiprocessing.get_context("spawn").Pool(procs) as pool:
+            secs = pool.map(_oracle_gemm_rows, bounds)
+        out["all_cores"] = {"value": 2 * n ** 3 / max(secs) / 1e12, "unit": "ring TOPS",
+                            "cores": procs,
+                            "sample": f"row blocks of the same GEMM, one process each "
+                                      f"(slowest {max(secs):.2f} s)"}
+    return out
+
+
+def oracle_resnet_measure(hws=ORACLE_RESNET_HW):
+    """One image of the private ResNet-18-shaped inference through the oracle at two
+    input resolutions (dealer included, weights shared beforehand); the time is
+    fitted as a + b * pixels and extrapolated to 224 x 224."""
+    from oracle import resnet as oresnet
+    sched = synth.resnet_schedule()
+    Wsh = oresnet.share_resnet_weights(synth.resnet_weights(), synth.RESNET18, sched)
+    secs = []
+    for hw in hws:
+        x = synth.resnet_input(batch=1, hw=hw)
+        t = time.perf_counter()
+        oresnet.private_resnet18(x, Wsh, synth.RESNET18, sched)
+        secs.append(time.perf_counter() - t)
+    (h0, h1), (t0, t1) = hws, secs
+    slope = (t1 - t0) / (h1 * h1 - h0 * h0)
+    t224 = t1 + slope * (224 * 224 - h1 * h1)
+    return {"value": 1 / t224, "unit": "images/s", "cores": 1, "kind": "oracle",
+            "extrapolated": True,
+            "sample": f"one image at {h0}x{h0} ({t0:.1f} s) and {h1}x{h1} ({t1:.1f} s), "
+                      f"time fitted linearly in pixels and extrapolated to 224x224 "
+                      f"({t224:.1f} s per image); numpy uint64 single-threaded"}
+
 
 def cpu_baseline_measure(steps=1, all_cores=True):
     t = time.perf_counter()
@@ -482,6 +542,10 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # host baseline: rank 0 at N = 1 only
         cpu = cpu_baseline_measure()
+        if not args.no_extras:
+            # the oracle on bounded samples of the ring GEMM and ResNet workloads
+            cpu["other_workloads"] = {"ring_gemm": oracle_gemm_measure(),
+                                      "resnet18": oracle_resnet_measure()}
 
     gemm_ms = busy["gemm_plain"] + busy["gemm_limb"]
     line = {
