@@ -202,6 +202,24 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
                           uint64_t* A, uint64_t* B, uint64_t* C, int algo, void* ws,
                           size_t ws_bytes, void* stream);
 
+/* A batch of `count` (1 <= count <= MPC_MAX_TRIPLE_BATCH) convolution triples
+ * of one descriptor d, triple j dealt at op id op_ids[j] into the caller's
+ * A[j], B[j], C[j] (device, shaped as for mpc_ttp_conv2d_triple): word for
+ * word what `count` calls of mpc_ttp_conv2d_triple give (the dealer's role
+ * in the paper's offline phase, §4).  On the limb engine the count
+ * products c_j = conv(a_j, b_j) run as the jobs of one GEMM launch after one
+ * digit-plane launch; on the plain engine the triples are dealt in turn.
+ * op_ids, A, B and C are host arrays of count entries.  ws: device workspace
+ * of mpc_conv2d_triples_workspace_size() bytes (0 for invalid arguments).
+ * Errors: MPC_EINVAL (party count, count, descriptor, null pointers),
+ * MPC_ENOMEM (workspace), MPC_EUNSUPPORTED (shape outside the limb engine). */
+#define MPC_MAX_TRIPLE_BATCH 8
+size_t mpc_conv2d_triples_workspace_size(int P, int count, const mpc_conv_desc* d, int algo);
+int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t seed,
+                           const uint64_t* op_ids, uint64_t* const* A, uint64_t* const* B,
+                           uint64_t* const* C, int algo, void* ws, size_t ws_bytes,
+                           void* stream);
+
 /* Binary AND triples for `gates` gates over n words: T device u64
  * [gates][3][P][n] holding (a, b, c) per gate, a and b from the AND_A/AND_B
  * streams (sub = gate), c = (xor_p a_p) & (xor_p b_p) shared with AND_C

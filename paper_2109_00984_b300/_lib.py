@@ -55,6 +55,9 @@ SIGNATURES = {
     "mpc_conv2d_triple_workspace_size": (c_size, [c_int, _P(ConvDesc), c_int]),
     "mpc_ttp_conv2d_triple": (c_int, [c_int, _P(ConvDesc), c_u64, c_u64, c_vp, c_vp, c_vp, c_int,
                                       c_vp, c_size, c_vp]),
+    "mpc_conv2d_triples_workspace_size": (c_size, [c_int, c_int, _P(ConvDesc), c_int]),
+    "mpc_ttp_conv2d_triples": (c_int, [c_int, c_int, _P(ConvDesc), c_u64, _P(c_u64), _P(c_vp),
+                                       _P(c_vp), _P(c_vp), c_int, c_vp, c_size, c_vp]),
     "mpc_ttp_and_triples": (c_int, [c_int, c_i64, c_int, c_u64, c_u64, c_vp, c_vp]),
     "mpc_ttp_b2a_bits": (c_int, [c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
     "mpc_beaver_mul": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int,

@@ -14,6 +14,7 @@ from . import _lib
 
 PLAIN, LIMB, AUTO = 0, 1, 2
 KS_GATES = 12
+MAX_TRIPLE_BATCH = 8   # mpc_ring.h MPC_MAX_TRIPLE_BATCH
 MAX_PARTIES = 8
 
 MPC_OK = 0
@@ -174,6 +175,29 @@ def ttp_conv2d_triple(P, d, seed, op_id, algo=PLAIN, device="cuda", out=None, ws
     _check(_L().mpc_ttp_conv2d_triple(P, ctypes.byref(d), seed, op_id, _ptr(A), _ptr(B), _ptr(C),
                                       algo, _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
     return A, B, C
+
+
+def conv2d_triples_workspace_size(P, count, d, algo=PLAIN):
+    return int(_L().mpc_conv2d_triples_workspace_size(P, count, ctypes.byref(d), algo))
+
+
+def ttp_conv2d_triples(P, d, seed, op_ids, algo=PLAIN, device="cuda", outs=None, ws=None):
+    """Convolution triples of one descriptor at each op id in `op_ids`
+    (mpc_ttp_conv2d_triples); outs: one (A, B, C) per op id, or None."""
+    count = len(op_ids)
+    ho, wo = conv_out_hw(d)
+    if outs is None:
+        outs = [(_words((P, d.batch, d.c_in, d.h, d.w), device),
+                 _words((P, d.c_out, d.c_in, d.kh, d.kw), device),
+                 _words((P, d.batch, d.c_out, ho, wo), device)) for _ in range(count)]
+    need = conv2d_triples_workspace_size(P, count, d, algo)
+    ws = _ws(need, device) if ws is None else ws
+    ids = (ctypes.c_uint64 * count)(*op_ids)
+    ptrs = [(ctypes.c_void_p * count)(*[_ptr(t[i]) for t in outs]) for i in range(3)]
+    _check(_L().mpc_ttp_conv2d_triples(P, count, ctypes.byref(d), seed, ids, ptrs[0], ptrs[1],
+                                       ptrs[2], algo, _ptr(ws, "ws", torch.uint8), ws.numel(),
+                                       _stream()))
+    return outs
 
 
 def ttp_and_triples(P, n, seed, op_id, gates=KS_GATES, device="cuda", out=None):

@@ -49,6 +49,10 @@ struct GemmArgs {
   int defer_reduce;
   u64* partial;
   const ConvGather* gather;  // host pointer; when set, B1/B2 are implicit im2col (limb only)
+  // With gather and one operand pair: job j's B1 is gathered from
+  // gather->src2[j] (no opening), one gather per job, instead of every job
+  // sharing the opened gather (the dealer's products of a batch of triples).
+  int gather_per_job;
   // Limb engine, convolution with gather only: digit planes cut ahead of the
   // call by limb_conv_prepare (layout in its comment).  The A operands and
   // every job's B2 are taken from there; only the opened gather B1 is cut in

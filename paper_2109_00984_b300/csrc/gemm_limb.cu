@@ -1509,6 +1509,9 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   if (prep && g.gather == nullptr)
     return fail(MPC_EINVAL, "limb engine: prepared planes need the convolution gather");
   const int npairs = (prep || g.jobs[0].A2) ? 2 : 1;
+  const bool per_job = g.gather != nullptr && g.gather_per_job != 0;
+  if (per_job && (npairs != 1 || prep))
+    return fail(MPC_EINVAL, "limb engine: per-job gathers take one-pair products");
   for (int j = 1; j < g.njobs && !prep; ++j)
     if ((g.jobs[j].A2 != nullptr) != (npairs == 2))
       return fail(MPC_EINVAL, "limb engine: jobs mix one- and two-pair products");
@@ -1553,7 +1556,17 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
       if (int rc = encode_planes(&prm.tmA[pr][j], ja.j[hit].out, g.M, K1p, BM)) return rc;
     }
   }
-  if (g.gather) {
+  int z0 = 0;  // first gather output cut by this call
+  if (per_job) {
+    // gather outputs 1 .. njobs: job j's B1 from src2[j]
+    z0 = 1;
+    nb = g.njobs;
+    for (int j = 0; j < g.njobs; ++j) {
+      jbv.j[1 + j] = PlaneJob{nullptr, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+      w += b_bytes;
+      if (int rc = encode_planes(&prm.tmB[0][j], jbv.j[1 + j].out, g.N, K1p, BN)) return rc;
+    }
+  } else if (g.gather) {
     // pair 1: the opened gather, shared; pair 2 (two-pair products): one per job
     nb = (npairs == 2 && !prep) ? 1 + g.njobs : 1;
     for (int z = 0; z < nb; ++z) {
@@ -1601,6 +1614,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     pl.Kp = K1p;
     pl.na = na;
     pl.nb = nb;
+    pl.z0 = z0;
     pl.bx = (int)ceil_div(K1p / KS, 8);  // B side: blocks of 8 sub-steps x 16 columns
     pl.by = (int)ceil_div(g.N, 16);
     // A side: about as many threads as 8-k groups, at most 4 blocks per SM and job.

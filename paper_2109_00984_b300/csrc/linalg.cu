@@ -121,13 +121,14 @@ int launch_fill_sum(int P, i64 n, u64 seed, u64 op_id, unsigned role, u64* Out, 
 // Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1 and C[P-1] =
 // c - sum_{p<P-1} C[p].  c is C[P-1] on entry, or, when the product's GEMM was
 // split along K (part != null), the sum of its `splits` partial sums
-// part[s][M][N] at the GEMM position of each output index (the NCHW scatter
-// of gemm_out_index when hw_out != 0): the reduction kernel is folded in.
+// part[s * pstride + row * N + col] at the GEMM position (row, col) of each
+// output index (the NCHW scatter of gemm_out_index when hw_out != 0): the
+// reduction kernel is folded in.
 __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u64 seed,
                                                                  u64 op_id, u64* __restrict__ C,
                                                                  const u64* __restrict__ part,
-                                                                 int splits, i64 M, i64 N,
-                                                                 i64 hw_out) {
+                                                                 i64 pstride, int splits, i64 M,
+                                                                 i64 N, i64 hw_out) {
   const i64 nblk = ceil_div(n, 4);
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
        t += (i64)gridDim.x * blockDim.x) {
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u
           col = i - row * N;
         }
         c = 0;
-        for (int sp = 0; sp < splits; ++sp) c += part[(i64)sp * M * N + row * N + col];
+        for (int sp = 0; sp < splits; ++sp) c += part[(i64)sp * pstride + row * N + col];
       } else {
         c = C[(i64)(P - 1) * n + i];
       }
@@ -167,14 +168,15 @@ __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u
   }
 }
 
-// The dealer's product c of a one-job GEMM set (as launched, splits deferred)
-// shared out as C.
-int share_product(int P, const GemmArgs& used, u64 seed, u64 op_id, u64* C, cudaStream_t s) {
+// The dealer's product c of job `job` of a GEMM set (as launched, splits
+// deferred: partial sums [splits][njobs][M][N]) shared out as C.
+int share_product(int P, const GemmArgs& used, u64 seed, u64 op_id, u64* C, cudaStream_t s,
+                  int job = 0) {
   const i64 n = used.M * used.N;
   const bool split = used.splits > 1;
   share_product_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(
-      P, n, seed, op_id, C, split ? used.partial : nullptr, split ? used.splits : 1, used.M,
-      used.N, used.hw_out);
+      P, n, seed, op_id, C, split ? used.partial + (i64)job * n : nullptr, (i64)used.njobs * n,
+      split ? used.splits : 1, used.M, used.N, used.hw_out);
   return check_launch("share product");
 }
 
@@ -721,6 +723,82 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   GemmArgs used{};
   if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, &used)) return rc;
   return share_product(P, used, seed, op_id, (u64*)C, s);
+}
+
+// A batch of `count` convolution triples of one shape.  On the limb engine
+// the count products c_j = conv(a_j, b_j) run as the jobs of one GEMM launch
+// (one digit-plane launch gathers every a_j); on the plain engine the
+// triples are dealt one by one.
+size_t mpc_conv2d_triples_workspace_size(int P, int count, const mpc_conv_desc* d, int algo) {
+  i64 ho, wo;
+  if (P < 1 || P > MPC_MAX_PARTIES || count < 1 || count > MPC_MAX_TRIPLE_BATCH ||
+      validate_conv(d, &ho, &wo) != MPC_OK)
+    return 0;
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  const i64 nx = d->batch * d->c_in * d->h * d->w;
+  algo = resolve_algo(algo, M, N, K);
+  if (algo != MPC_ALGO_LIMB || !limb_supported(M, N, K)) return conv_triple_ws(*d, ho, wo, algo);
+  return (size_t)count * (align256(words(nx)) + align256(words(M * K))) +
+         engine_ws(MPC_ALGO_LIMB, M, N, K, 1, count);
+}
+
+int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t seed,
+                           const uint64_t* op_ids, uint64_t* const* A, uint64_t* const* B,
+                           uint64_t* const* C, int algo, void* ws, size_t ws_bytes,
+                           void* stream) {
+  MPC_CHECK_PARTIES(P);
+  if (int rc = check_algo(algo)) return rc;
+  MPC_REQUIRE(count >= 1 && count <= MPC_MAX_TRIPLE_BATCH, "count %d outside [1, %d]", count,
+              MPC_MAX_TRIPLE_BATCH);
+  i64 ho, wo;
+  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  MPC_REQUIRE(op_ids && A && B && C, "null pointer");
+  for (int j = 0; j < count; ++j) MPC_REQUIRE(A[j] && B[j] && C[j], "null pointer (triple %d)", j);
+  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
+  const i64 nx = d->batch * d->c_in * d->h * d->w;
+  algo = resolve_algo(algo, M, N, K);
+  if (algo != MPC_ALGO_LIMB || count == 1) {
+    for (int j = 0; j < count; ++j)
+      if (int rc = mpc_ttp_conv2d_triple(P, d, seed, op_ids[j], A[j], B[j], C[j], algo, ws,
+                                         ws_bytes, stream))
+        return rc;
+    return MPC_OK;
+  }
+  if (!limb_supported(M, N, K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
+  const size_t need = mpc_conv2d_triples_workspace_size(P, count, d, algo);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  ConvGather cg{};
+  cg.d = *d;
+  cg.ho = ho;
+  cg.wo = wo;
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.hw_out = ho * wo;
+  g.njobs = count;
+  g.gather = &cg;
+  g.gather_per_job = 1;
+  g.defer_reduce = 1;  // the correction kernels add the split-K partial sums themselves
+  for (int j = 0; j < count; ++j) {
+    u64* a = cv.take(nx);
+    u64* b = cv.take(M * K);
+    if (int rc = launch_fill_sum(P, nx, seed, op_ids[j], MPC_ROLE_TRIPLE_A, (u64*)A[j], a, s))
+      return rc;
+    if (int rc = launch_fill_sum(P, M * K, seed, op_ids[j], MPC_ROLE_TRIPLE_B, (u64*)B[j], b, s))
+      return rc;
+    cg.src2[j] = a;
+    g.jobs[j] = GemmJob{b, nullptr, nullptr, nullptr, nullptr, (u64*)C[j] + (i64)(P - 1) * M * N};
+  }
+  GemmArgs used{};
+  if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, &used)) return rc;
+  for (int j = 0; j < count; ++j)
+    if (int rc = share_product(P, used, seed, op_ids[j], (u64*)C[j], s, j)) return rc;
+  return MPC_OK;
 }
 
 }  // extern "C"

@@ -28,12 +28,19 @@ import torch
 from . import api
 
 
+def _same_desc(a, b):
+    return all(getattr(a, f) == getattr(b, f) for f, _ in a._fields_)
+
+
 class PrivateConv1dStack:
     def __init__(self, weights, strides, pads, frames, batch=1, algo=api.PLAIN, frac_bits=16,
                  weight_ops=None, seed=1, device="cuda", fused_relu=True, overlap_dealer=True,
-                 prepare_weights=False):
+                 prepare_weights=False, batch_triples=True):
         self.P = 2
         self.fused_relu = fused_relu
+        # deal the triples of consecutive same-shaped layers in one batched call
+        # (one GEMM launch for all their products on the limb engine)
+        self.batch_triples = batch_triples
         self.overlap_dealer = overlap_dealer
         self.algo = algo
         self.frac_bits = frac_bits
@@ -87,6 +94,18 @@ class PrivateConv1dStack:
             C=torch.empty((P, d.batch, d.c_out) + tuple(api.conv_out_hw(d)), dtype=torch.int64,
                           device=dev)) for d in self.descs] for _ in range(2)]
         self.ready = [[None] * len(self.descs) for _ in range(2)]
+        # runs of consecutive layers with one descriptor: (first layer, count)
+        self.deal_groups = []
+        for l, d in enumerate(self.descs):
+            g = self.deal_groups[-1] if self.deal_groups else None
+            if (self.batch_triples and g is not None and g[1] < api.MAX_TRIPLE_BATCH and
+                    _same_desc(self.descs[g[0]], d)):
+                self.deal_groups[-1] = (g[0], g[1] + 1)
+            else:
+                self.deal_groups.append((l, 1))
+        for first, count in self.deal_groups:
+            ws_bytes = max(ws_bytes, api.conv2d_triples_workspace_size(P, count, self.descs[first],
+                                                                      self.algo))
         self.prepared = False
         self.prep = None
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -126,19 +145,28 @@ class PrivateConv1dStack:
         ds = self.dealer_stream if self.overlap_dealer else main
         if ds is not main:
             ds.wait_stream(main)
+        ws = self.dealer_ws if ds is not main else self.ws
         with torch.cuda.stream(ds):
-            for l, d in enumerate(self.descs):
-                t = self.trip[slot][l]
-                api.ttp_conv2d_triple(self.P, d, seed, schedule["layers"][l]["conv"], self.algo,
-                                      out=(t["A"], t["B"], t["C"]),
-                                      ws=self.dealer_ws if ds is not main else self.ws)
-                if self.prepared:
-                    api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], d,
-                                              out=self.prep[slot][l])
-                if ds is not main:
-                    ev = torch.cuda.Event()
-                    ev.record(ds)
-                    self.ready[slot][l] = ev
+            for first, count in self.deal_groups:
+                layers = range(first, first + count)
+                outs = [(self.trip[slot][l]["A"], self.trip[slot][l]["B"], self.trip[slot][l]["C"])
+                        for l in layers]
+                ops = [schedule["layers"][l]["conv"] for l in layers]
+                if count == 1:
+                    api.ttp_conv2d_triple(self.P, self.descs[first], seed, ops[0], self.algo,
+                                          out=outs[0], ws=ws)
+                else:
+                    api.ttp_conv2d_triples(self.P, self.descs[first], seed, ops, self.algo,
+                                           outs=outs, ws=ws)
+                for l in layers:
+                    t = self.trip[slot][l]
+                    if self.prepared:
+                        api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], self.descs[l],
+                                                  out=self.prep[slot][l])
+                    if ds is not main:
+                        ev = torch.cuda.Event()
+                        ev.record(ds)
+                        self.ready[slot][l] = ev
         if join and ds is not main:
             main.wait_stream(ds)
 

@@ -138,6 +138,30 @@ def test_beaver_conv2d_limb(mpc, geom, P, rng):
     assert np.array_equal(host(gC), C)
 
 
+@pytest.mark.parametrize("P", [2, 3])
+@pytest.mark.parametrize("engine", ["limb", "plain"])
+@pytest.mark.parametrize("geom", [
+    # (batch, c_in, h, w, c_out, kh, kw, stride, pad_h, pad_w)
+    (2, 16, 9, 11, 24, 3, 3, 2, 1, 1),     # ragged tiles, one split
+    (1, 128, 1, 100, 40, 1, 7, 1, 0, 3),   # K = 896: the batched GEMM is split along K
+])
+def test_conv_triples_batch_matches_oracle(mpc, P, engine, geom):
+    """A batch of same-shaped convolution triples (one GEMM launch for all their
+    products on the limb engine) equals the oracle's triples at each op id."""
+    b, ci, h, w, co, kh, kw, st, ph, pw = geom
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    ops = [70, 81, 92]
+    algo = mpc.LIMB if engine == "limb" else mpc.PLAIN
+    outs = mpc.ttp_conv2d_triples(P, d, SEED, ops, algo=algo)
+    mpc.sync_status()
+    for op, (gA, gB, gC) in zip(ops, outs):
+        rA, rB, rC = dealer.conv2d_triple(P, (b, ci, h, w), (co, ci, kh, kw), st, ph, SEED, op,
+                                          pad_w=pw)
+        assert np.array_equal(host(gA), rA)
+        assert np.array_equal(host(gB), rB)
+        assert np.array_equal(host(gC), rC)
+
+
 def test_limb_large_subset(mpc, rng):
     """A 1024^3 product checked on a 64 x 64 sample of outputs with full K."""
     n = 1024
