@@ -64,19 +64,42 @@ class PrivateResNet18:
         return api.ttp_conv2d_triple(self.P, d, self.seed, op, self.algo, device=self.device, ws=ws)
 
     def _deal_all(self, x_shape, schedule):
-        """Walk the network's shapes and deal every conv / FC triple in order."""
+        """Walk the network's shapes and deal every conv / FC triple in order;
+        the triples of consecutive same-shaped convolutions are dealt in one
+        batched call (one GEMM launch for their products on the limb engine)."""
         ops = schedule["ops"]
         triples = {}
         N, _, H, W = x_shape
         C = 3
+        pending = []   # (key, desc) of consecutive same-shaped convolutions
+
+        def flush():
+            if not pending:
+                return
+            d = pending[0][1]
+            keys = [k for k, _ in pending]
+            if len(keys) == 1:
+                ws = self._dealer_ws(api.conv2d_triple_workspace_size(self.P, d, self.algo))
+                got = [self._deal_conv(d, ops[keys[0]], ws)]
+            else:
+                ws = self._dealer_ws(api.conv2d_triples_workspace_size(self.P, len(keys), d,
+                                                                       self.algo))
+                got = api.ttp_conv2d_triples(self.P, d, self.seed, [ops[k] for k in keys],
+                                             self.algo, device=self.device, ws=ws)
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream())
+            for k, t in zip(keys, got):
+                triples[k] = t
+                triples[k + "#ev"] = ev
+            pending.clear()
 
         def conv(name, cin, cout, k, stride, pad, h, w, key):
             d = api.conv_desc(N, cin, h, w, cout, k, k, stride, stride, pad, pad)
-            ws = self._dealer_ws(api.conv2d_triple_workspace_size(self.P, d, self.algo))
-            triples[key] = self._deal_conv(d, ops[key], ws)
-            ev = torch.cuda.Event()
-            ev.record(torch.cuda.current_stream())
-            triples[key + "#ev"] = ev
+            if pending and (len(pending) == api.MAX_TRIPLE_BATCH or
+                            not all(getattr(d, f) == getattr(pending[0][1], f)
+                                    for f, _ in d._fields_)):
+                flush()
+            pending.append((key, d))
             return api.conv_out_hw(d)
 
         for layer in self.layers:
@@ -95,12 +118,14 @@ class PrivateResNet18:
                     conv(name, cin, cout, 1, s, 0, H, W, name + ".down")
                 H, W, C = h1, w1, cout
             elif kind == "fc":
+                flush()
                 cin, cout = layer[2], layer[3]
                 triples[name] = api.ttp_matmul_triple(self.P, N, cout, cin, self.seed, ops[name],
                                                       self.algo, device=self.device)
                 ev = torch.cuda.Event()
                 ev.record(torch.cuda.current_stream())
                 triples[name + "#ev"] = ev
+        flush()
         return triples
 
     def _triple(self, key):
