@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # products), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
 # on the current kernel; and the digit-plane bytes those launches must read
 # (785.5 MB per step: 16 bytes per operand word).
-LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 95.4e6
+LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 97.4e6
 LIMB_GEMM_PLANE_BYTES_PER_LAUNCH = 87.3e6
 # ncu sm__pipe_tensor_cycles_active (% of elapsed cycles) of the same kernel in
 # one capture each: an online speech-layer launch, and the 4096^3 ring GEMM.

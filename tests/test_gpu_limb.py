@@ -143,7 +143,7 @@ def test_beaver_conv2d_limb(mpc, geom, P, rng):
 @pytest.mark.parametrize("geom", [
     # (batch, c_in, h, w, c_out, kh, kw, stride, pad_h, pad_w)
     (2, 16, 9, 11, 24, 3, 3, 2, 1, 1),     # ragged tiles, one split
-    (1, 128, 1, 100, 40, 1, 7, 1, 0, 3),   # K = 896: the batched GEMM is split along K
+    (1, 160, 1, 100, 40, 1, 7, 1, 0, 3),   # K = 1120: the batched GEMM is split along K
 ])
 def test_conv_triples_batch_matches_oracle(mpc, P, engine, geom):
     """A batch of same-shaped convolution triples (one GEMM launch for all their
