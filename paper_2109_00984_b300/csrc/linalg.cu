@@ -104,6 +104,44 @@ __global__ void __launch_bounds__(kThreads) fill_sum2_kernel(i64 n, u64 seed, u6
   }
 }
 
+// Several two-party dealer fills in one launch (the A and B fills of a batch
+// of triples): segment q is fill_sum2_kernel's work for (n, op_id, role, Out,
+// sum) of that segment; each segment's lanes are rounded up to whole warps so
+// that a warp stays in one segment.
+constexpr int kMaxFillSegs = 2 * MPC_MAX_TRIPLE_BATCH;
+struct FillSegs {
+  u64* Out[kMaxFillSegs];
+  u64* sum[kMaxFillSegs];
+  i64 n[kMaxFillSegs];
+  u64 op_id[kMaxFillSegs];
+  unsigned role[kMaxFillSegs];
+  i64 base[kMaxFillSegs + 1];  // first lane of each segment (multiples of 32), then the total
+  int count;
+};
+
+__global__ void __launch_bounds__(kThreads) fill_sum2_multi_kernel(const __grid_constant__ FillSegs f,
+                                                                   u64 seed) {
+  const int lane = threadIdx.x & 31, p = lane & 1;
+  const i64 wstride = (i64)gridDim.x * blockDim.x;
+  for (i64 wb = (blockIdx.x * (i64)blockDim.x + threadIdx.x) - lane; wb < f.base[f.count];
+       wb += wstride) {
+    int q = 0;
+    while (wb >= f.base[q + 1]) ++q;
+    const i64 n = f.n[q], nblk = ceil_div(n, 4);
+    const i64 t = (wb - f.base[q] + lane) >> 1;
+    const bool valid = t < nblk;
+    const u64x4 r = prg_block(seed, f.op_id[q], stream_word2(f.role[q], 0, p), valid ? t : 0);
+    const i64 i0 = 4 * t;
+    if (valid) store4(f.Out[q] + (i64)p * n, i0, n, as_quad(r));
+    if (f.sum[q]) {
+      Quad s4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s4.v[j] = r.v[j] + __shfl_xor_sync(0xffffffffu, r.v[j], 1);
+      if (valid && p == 0) store4(f.sum[q], i0, n, s4);
+    }
+  }
+}
+
 // Launches the dealer fill (two parties: fill_sum2_kernel).
 int launch_fill_sum(int P, i64 n, u64 seed, u64 op_id, unsigned role, u64* Out, u64* sum,
                     cudaStream_t s) {
@@ -117,18 +155,65 @@ int launch_fill_sum(int P, i64 n, u64 seed, u64 op_id, unsigned role, u64* Out, 
   return check_launch("dealer fill");
 }
 
+// The dealer fills of segments q < count (Out[q], sum[q], n[q], op_id[q],
+// role[q]): one launch for two parties, one per segment otherwise.
+int launch_fill_multi(int P, int count, u64* const* Out, u64* const* sum, const i64* n,
+                      const u64* op_id, const unsigned* role, u64 seed, cudaStream_t s) {
+  if (P != 2 || count > kMaxFillSegs) {
+    for (int q = 0; q < count; ++q)
+      if (int rc = launch_fill_sum(P, n[q], seed, op_id[q], role[q], Out[q], sum[q], s)) return rc;
+    return MPC_OK;
+  }
+  FillSegs f;
+  memset(&f, 0, sizeof(f));
+  f.count = count;
+  for (int q = 0; q < count; ++q) {
+    f.Out[q] = Out[q];
+    f.sum[q] = sum[q];
+    f.n[q] = n[q];
+    f.op_id[q] = op_id[q];
+    f.role[q] = role[q];
+    f.base[q + 1] = f.base[q] + ceil_div(2 * ceil_div(n[q], 4), 32) * 32;
+  }
+  if (f.base[count] == 0) return MPC_OK;
+  fill_sum2_multi_kernel<<<grid_for(f.base[count], kThreads), kThreads, 0, s>>>(f, seed);
+  return check_launch("dealer fill");
+}
+
+// A triple's two fills (A with its sum a over nA words, B with b over nB).
+int launch_fill_pair(int P, u64 seed, u64 op_id, u64* A, u64* a, i64 nA, u64* B, u64* b, i64 nB,
+                     cudaStream_t s) {
+  u64* out[2] = {A, B};
+  u64* sum[2] = {a, b};
+  const i64 n[2] = {nA, nB};
+  const u64 op[2] = {op_id, op_id};
+  const unsigned role[2] = {MPC_ROLE_TRIPLE_A, MPC_ROLE_TRIPLE_B};
+  return launch_fill_multi(P, 2, out, sum, n, op, role, seed, s);
+}
+
 
 // Dealer correction: C[p] = stream(TRIPLE_C, p) for p < P-1 and C[P-1] =
 // c - sum_{p<P-1} C[p].  c is C[P-1] on entry, or, when the product's GEMM was
 // split along K (part != null), the sum of its `splits` partial sums
 // part[s * pstride + row * N + col] at the GEMM position (row, col) of each
 // output index (the NCHW scatter of gemm_out_index when hw_out != 0): the
-// reduction kernel is folded in.
+// reduction kernel is folded in.  blockIdx.y is the job j of a batch of
+// products: C = Cs.C[j], op_id = Cs.op_id[j], part + j n.
+struct ShareJobs {
+  u64* C[MPC_MAX_TRIPLE_BATCH];
+  u64 op_id[MPC_MAX_TRIPLE_BATCH];
+};
+
 __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u64 seed,
-                                                                 u64 op_id, u64* __restrict__ C,
-                                                                 const u64* __restrict__ part,
+                                                                 const __grid_constant__ ShareJobs
+                                                                     Cs,
+                                                                 const u64* __restrict__ part0,
                                                                  i64 pstride, int splits, i64 M,
                                                                  i64 N, i64 hw_out) {
+  const int job = blockIdx.y;
+  u64* __restrict__ C = Cs.C[job];
+  const u64 op_id = Cs.op_id[job];
+  const u64* __restrict__ part = part0 ? part0 + (i64)job * n : nullptr;
   const i64 nblk = ceil_div(n, 4);
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < nblk;
        t += (i64)gridDim.x * blockDim.x) {
@@ -168,16 +253,29 @@ __global__ void __launch_bounds__(kThreads) share_product_kernel(int P, i64 n, u
   }
 }
 
-// The dealer's product c of job `job` of a GEMM set (as launched, splits
-// deferred: partial sums [splits][njobs][M][N]) shared out as C.
-int share_product(int P, const GemmArgs& used, u64 seed, u64 op_id, u64* C, cudaStream_t s,
-                  int job = 0) {
+// The dealer's products c_j of the jobs j < used.njobs of a GEMM set (as
+// launched, splits deferred: partial sums [splits][njobs][M][N]) shared out as
+// C[j] with op ids op_id[j], in one launch.
+int share_products(int P, const GemmArgs& used, u64 seed, const u64* op_id, u64* const* C,
+                   cudaStream_t s) {
   const i64 n = used.M * used.N;
   const bool split = used.splits > 1;
-  share_product_kernel<<<grid_for(ceil_div(n, 4), kThreads), kThreads, 0, s>>>(
-      P, n, seed, op_id, C, split ? used.partial + (i64)job * n : nullptr, (i64)used.njobs * n,
-      split ? used.splits : 1, used.M, used.N, used.hw_out);
+  ShareJobs Cs;
+  memset(&Cs, 0, sizeof(Cs));
+  for (int j = 0; j < used.njobs; ++j) {
+    Cs.C[j] = C[j];
+    Cs.op_id[j] = op_id[j];
+  }
+  const dim3 grid(grid_for(ceil_div(n, 4), kThreads, 148 * 32 / used.njobs), used.njobs);
+  share_product_kernel<<<grid, kThreads, 0, s>>>(P, n, seed, Cs, split ? used.partial : nullptr,
+                                                 (i64)used.njobs * n, split ? used.splits : 1,
+                                                 used.M, used.N, used.hw_out);
   return check_launch("share product");
+}
+
+// The same for a one-job GEMM set.
+int share_product(int P, const GemmArgs& used, u64 seed, u64 op_id, u64* C, cudaStream_t s) {
+  return share_products(P, used, seed, &op_id, &C, s);
 }
 
 // im2col over the ring: col[k][c] with k = (ci * kh + r) * kw + s and
@@ -653,8 +751,7 @@ int mpc_ttp_matmul_triple(int P, int64_t M, int64_t N, int64_t K, uint64_t seed,
   Carve cv(ws);
   u64* a = cv.take(M * K);
   u64* b = cv.take(K * N);
-  if (int rc = launch_fill_sum(P, M * K, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a, s)) return rc;
-  if (int rc = launch_fill_sum(P, K * N, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b, s)) return rc;
+  if (int rc = launch_fill_pair(P, seed, op_id, (u64*)A, a, M * K, (u64*)B, b, K * N, s)) return rc;
   if (M * N == 0) return MPC_OK;
   u64* Clast = (u64*)C + (i64)(P - 1) * M * N;
   GemmArgs g{};
@@ -698,8 +795,7 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   u64* a = cv.take(nx);
   u64* acol = gather ? nullptr : cv.take(K * N);
   u64* b = cv.take(M * K);
-  if (int rc = launch_fill_sum(P, nx, seed, op_id, MPC_ROLE_TRIPLE_A, (u64*)A, a, s)) return rc;
-  if (int rc = launch_fill_sum(P, M * K, seed, op_id, MPC_ROLE_TRIPLE_B, (u64*)B, b, s)) return rc;
+  if (int rc = launch_fill_pair(P, seed, op_id, (u64*)A, a, nx, (u64*)B, b, M * K, s)) return rc;
   ConvGather cg{};
   if (gather) {
     cg.d = *d;
@@ -784,21 +880,41 @@ int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t se
   g.gather = &cg;
   g.gather_per_job = 1;
   g.defer_reduce = 1;  // the correction kernels add the split-K partial sums themselves
+  // The fills, one launch each: a single launch for all of them made the dealer
+  // alone 7 % faster but the overlapped speech step 1 % slower (one wide
+  // launch takes every SM from the online phase at once; small ones fit in
+  // its gaps).
+  u64* fout[2 * MPC_MAX_TRIPLE_BATCH];
+  u64* fsum[2 * MPC_MAX_TRIPLE_BATCH];
+  i64 fn[2 * MPC_MAX_TRIPLE_BATCH];
+  u64 fop[2 * MPC_MAX_TRIPLE_BATCH];
+  unsigned frole[2 * MPC_MAX_TRIPLE_BATCH];
   for (int j = 0; j < count; ++j) {
     u64* a = cv.take(nx);
     u64* b = cv.take(M * K);
-    if (int rc = launch_fill_sum(P, nx, seed, op_ids[j], MPC_ROLE_TRIPLE_A, (u64*)A[j], a, s))
-      return rc;
-    if (int rc = launch_fill_sum(P, M * K, seed, op_ids[j], MPC_ROLE_TRIPLE_B, (u64*)B[j], b, s))
-      return rc;
+    fout[2 * j] = (u64*)A[j];
+    fsum[2 * j] = a;
+    fn[2 * j] = nx;
+    frole[2 * j] = MPC_ROLE_TRIPLE_A;
+    fout[2 * j + 1] = (u64*)B[j];
+    fsum[2 * j + 1] = b;
+    fn[2 * j + 1] = M * K;
+    frole[2 * j + 1] = MPC_ROLE_TRIPLE_B;
+    fop[2 * j] = fop[2 * j + 1] = op_ids[j];
     cg.src2[j] = a;
     g.jobs[j] = GemmJob{b, nullptr, nullptr, nullptr, nullptr, (u64*)C[j] + (i64)(P - 1) * M * N};
   }
+  for (int q = 0; q < 2 * count; ++q)
+    if (int rc = launch_fill_sum(P, fn[q], seed, fop[q], frole[q], fout[q], fsum[q], s)) return rc;
   GemmArgs used{};
   if (int rc = run_gemm(g, algo, cv.rest(), ws_bytes - cv.off, s, &used)) return rc;
-  for (int j = 0; j < count; ++j)
-    if (int rc = share_product(P, used, seed, op_ids[j], (u64*)C[j], s, j)) return rc;
-  return MPC_OK;
+  u64* Cs[MPC_MAX_TRIPLE_BATCH];
+  u64 ops[MPC_MAX_TRIPLE_BATCH];
+  for (int j = 0; j < count; ++j) {
+    Cs[j] = (u64*)C[j];
+    ops[j] = op_ids[j];
+  }
+  return share_products(P, used, seed, ops, Cs, s);
 }
 
 }  // extern "C"
