@@ -309,8 +309,11 @@ def run_ours(args):
 
     x, ws, strides, pads = synth.speech_stack(seed=rank)
     sched0 = synth.speech_schedule(len(ws), step=0)
+    # The dealer also prepares each convolution's input-independent half (F = W - B
+    # opened, the weight-side and im2col(A_p) digit planes) for the online phase.
     net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=1, algo=algo,
-                             weight_ops=sched0["weight_op"], seed=sched0["seed"], device=dev)
+                             weight_ops=sched0["weight_op"], seed=sched0["seed"], device=dev,
+                             prepare_weights=True)
     x_dev = torch.from_numpy(x).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -456,24 +459,26 @@ def run_ours(args):
         phases = {"online_only_ms": median_event_ms(g_on.replay, args.steps, flush, warm=2),
                   "dealer_only_ms": median_event_ms(g_deal.replay, args.steps, flush, warm=2),
                   "pipelined_step_ms": float(np.median(step_ms)),
-                  "note": "online phase of one forward on triples dealt beforehand, and one "
-                          "forward's dealing, each alone as a graph replay; the timed steps "
+                  "note": "online phase of one forward on triples dealt (and convolutions "
+                          "prepared) beforehand, and one forward's dealing with the "
+                          "preparation, each alone as a graph replay; the timed steps "
                           "overlap the two on two streams"}
         del g_on, g_deal
-        # The same with the convolutions' input-independent half (F = W - B
-        # opened, weight-side and im2col(A_p) planes) moved to the dealer: the
-        # online phase's latency, not used for the throughput steps above.
-        net.enable_prepared(True)
-        if net.prepared:
+        # The same with the convolutions' input-independent half left in the
+        # online phase (no prepared planes): the split the timed steps do not use.
+        was_prepared = net.prepared
+        net.enable_prepared(not was_prepared)
+        if net.prepared != was_prepared:
+            key = "prepared" if net.prepared else "unprepared"
             net.deal(sch, 0, join=True)
             g_on = phase_graph(lambda: net.reveal(net.online(x_dev, sch, 0, wait_dealer=False)))
             g_deal = phase_graph(lambda: net.deal(sch, 1, join=True))
-            phases["online_only_prepared_ms"] = median_event_ms(g_on.replay, args.steps, flush,
-                                                                warm=2)
-            phases["dealer_only_prepared_ms"] = median_event_ms(g_deal.replay, args.steps, flush,
-                                                                warm=2)
+            phases[f"online_only_{key}_ms"] = median_event_ms(g_on.replay, args.steps, flush,
+                                                              warm=2)
+            phases[f"dealer_only_{key}_ms"] = median_event_ms(g_deal.replay, args.steps, flush,
+                                                              warm=2)
             del g_on, g_deal
-        net.enable_prepared(False)
+        net.enable_prepared(was_prepared)
 
     if rank != 0:
         if world > 1:

@@ -125,8 +125,9 @@ class PrivateConv1dStack:
         of im2col(A_p) -- is done by the dealer right after the layer's triple,
         into a prepared-plane buffer per layer and triple slot, and the online
         phase only cuts im2col(E) before its GEMM.  That shortens the online
-        phase (its latency); with the dealer overlapped the total work is the
-        same, so it does not raise throughput.  Takes effect from the next deal."""
+        phase (its latency) and, with the dealer's triples batched, also raises
+        the overlapped throughput (the dealer's launches fit the online phase's
+        gaps).  Takes effect from the next deal."""
         ok = on and self.fused_relu and self.algo != api.PLAIN and all(
             api.conv2d_prep_size(self.P, d) > 0 for d in self.descs)
         if ok and self.prep is None:
