@@ -26,9 +26,13 @@ from . import api
 
 class PrivateResNet18:
     def __init__(self, weights, layers, schedule, algo=api.AUTO, frac_bits=16, device="cuda",
-                 fused_relu=True, overlap_dealer=True):
+                 fused_relu=True, overlap_dealer=True, prepare_weights=False):
         self.P = 2
         self.fused_relu = fused_relu
+        # With prepare_weights (limb engine, fused ReLU) the dealer also does each
+        # convolution's input-independent half (F = W - B opened, the weight-side
+        # and im2col(A_p) digit planes) right after its triple.
+        self.prepare = prepare_weights and fused_relu and algo != api.PLAIN
         self.overlap_dealer = overlap_dealer
         # Online phase on a high-priority stream, dealer on a low-priority one.
         self.dealer_stream = torch.cuda.Stream(device=device, priority=0) if overlap_dealer \
@@ -86,10 +90,13 @@ class PrivateResNet18:
                                                                        self.algo))
                 got = api.ttp_conv2d_triples(self.P, d, self.seed, [ops[k] for k in keys],
                                              self.algo, device=self.device, ws=ws)
-            ev = torch.cuda.Event()
-            ev.record(torch.cuda.current_stream())
             for k, t in zip(keys, got):
                 triples[k] = t
+                if self.prepare and api.conv2d_prep_size(self.P, d) > 0:
+                    triples[k + "#prep"] = api.beaver_conv2d_prepare(self.W[k], t[0], t[1], d)
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream())
+            for k in keys:
                 triples[k + "#ev"] = ev
             pending.clear()
 
@@ -138,6 +145,13 @@ class PrivateResNet18:
             tensor.record_stream(main)
         return t
 
+    def _prep(self, key):
+        """The prepared planes of convolution `key` (after _triple), or None."""
+        prep = self._triples.get(key + "#prep") if key is not None else None
+        if prep is not None:
+            prep.record_stream(torch.cuda.current_stream())
+        return prep
+
     # ---- layer operations ---------------------------------------------------------
     def conv(self, X, Wsh, stride, pad, op, key=None):
         P, N, Cin, H, W = X.shape
@@ -149,6 +163,10 @@ class PrivateResNet18:
                               api.conv2d_triple_workspace_size(P, d, self.algo)))
             trip = self._deal_conv(d, op, ws)
         A, B, C = trip
+        prep = self._prep(key)
+        if prep is not None:
+            ws = self._ws(api.conv2d_workspace_size(P, d, api.LIMB))
+            return api.beaver_conv2d_prepared(X, A, C, prep, d, self.frac_bits, ws=ws)
         ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d(X, Wsh, A, B, C, d, self.algo, self.frac_bits, ws=ws)
 
@@ -166,6 +184,11 @@ class PrivateResNet18:
                               api.conv2d_triple_workspace_size(P, d, self.algo)))
             trip = self._deal_conv(d, op, ws)
         A, B, C = trip
+        prep = self._prep(key)
+        if prep is not None:
+            ws = self._ws(api.conv2d_workspace_size(P, d, api.LIMB))
+            return api.beaver_conv2d_relu_prepared(X, A, C, prep, d, self.seed, relu_op,
+                                                   self.frac_bits, ws=ws)
         ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d_relu(X, Wsh, A, B, C, d, self.seed, relu_op, self.algo,
                                       self.frac_bits, ws=ws)

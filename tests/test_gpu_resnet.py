@@ -63,12 +63,12 @@ def test_maxpool_tree(mpc, rng):
     assert np.array_equal(got, ref)
 
 
-def _gpu_forward(mpc, x, algo=None, fused=True):
+def _gpu_forward(mpc, x, algo=None, fused=True, prepared=False):
     from paper_2109_00984_b300.resnet import PrivateResNet18
     W = synth.resnet_weights()
     sched = synth.resnet_schedule()
     net = PrivateResNet18(W, synth.RESNET18, sched, algo=mpc.AUTO if algo is None else algo,
-                          fused_relu=fused)
+                          fused_relu=fused, prepare_weights=prepared)
     Y = net.forward(dev_f64(x), sched)
     real = net.reveal(Y)
     torch.cuda.synchronize()
@@ -87,6 +87,16 @@ def _oracle_forward(x):
 def test_small_resnet_bit_exact(mpc, engine, fused):
     x = synth.resnet_input(batch=2, hw=32)
     got, got_real = _gpu_forward(mpc, x, mpc.PLAIN if engine == "plain" else mpc.AUTO, fused)
+    ref, ref_real, _ = _oracle_forward(x)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(got_real, ref_real)
+
+
+def test_small_resnet_prepared_bit_exact(mpc):
+    """The dealer also prepares every convolution's input-independent half; the
+    online phase runs the prepared convolutions: the same words."""
+    x = synth.resnet_input(batch=2, hw=32)
+    got, got_real = _gpu_forward(mpc, x, prepared=True)
     ref, ref_real, _ = _oracle_forward(x)
     assert np.array_equal(got, ref)
     assert np.array_equal(got_real, ref_real)
