@@ -106,7 +106,7 @@ def test_small_resnet_prepared_bit_exact(mpc):
 def test_full_resnet_image0_bit_exact(mpc):
     """Batch 8 x 224 x 224 (the bench configuration); image 0 against the oracle."""
     x = synth.resnet_input(batch=8, hw=224)
-    got, got_real = _gpu_forward(mpc, x)
+    got, got_real = _gpu_forward(mpc, x, prepared=True)   # the bench's configuration
     ref, ref_real, W = _oracle_forward(x[:1])
     assert np.array_equal(got[:, :1], ref)
     plain = oresnet.plaintext_resnet18(x, W, synth.RESNET18)
@@ -114,12 +114,14 @@ def test_full_resnet_image0_bit_exact(mpc):
     assert nmse < 4e-4
 
 
-def test_small_resnet_graph_replay_bit_exact(mpc):
+@pytest.mark.parametrize("prepared", [False, True])
+def test_small_resnet_graph_replay_bit_exact(mpc, prepared):
     """The bench's timed path: a captured forward + reveal, replayed, equals the oracle."""
     from paper_2109_00984_b300.resnet import PrivateResNet18
     x = synth.resnet_input(batch=2, hw=32)
     sched = synth.resnet_schedule(step=4)
-    net = PrivateResNet18(synth.resnet_weights(), synth.RESNET18, sched, algo=mpc.AUTO)
+    net = PrivateResNet18(synth.resnet_weights(), synth.RESNET18, sched, algo=mpc.AUTO,
+                          prepare_weights=prepared)
     xd = dev_f64(x)
     net.reveal(net.forward(xd, synth.resnet_schedule(step=9)))   # warm-up sizes the workspaces
     (g, out), = net.capture(xd, [sched])
