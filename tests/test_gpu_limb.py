@@ -162,6 +162,22 @@ def test_conv_triples_batch_matches_oracle(mpc, P, engine, geom):
         assert np.array_equal(host(gC), rC)
 
 
+@pytest.mark.parametrize("P,count", [(8, 2), (2, 8)])
+def test_conv_triples_batch_edges(mpc, P, count):
+    """Eight parties, and the largest batch, on a tiny convolution (N = 15 output
+    columns, M = 8 rows: one ragged tile per product)."""
+    b, ci, h, w, co, kh, kw, st, ph, pw = (1, 16, 3, 5, 8, 3, 3, 1, 1, 1)
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    ops = [300 + 7 * j for j in range(count)]
+    outs = mpc.ttp_conv2d_triples(P, d, SEED, ops, algo=mpc.LIMB)
+    mpc.sync_status()
+    for op, (gA, gB, gC) in zip(ops, outs):
+        rA, rB, rC = dealer.conv2d_triple(P, (b, ci, h, w), (co, ci, kh, kw), st, ph, SEED, op,
+                                          pad_w=pw)
+        assert np.array_equal(host(gA), rA) and np.array_equal(host(gB), rB)
+        assert np.array_equal(host(gC), rC)
+
+
 def test_limb_large_subset(mpc, rng):
     """A 1024^3 product checked on a 64 x 64 sample of outputs with full K."""
     n = 1024
