@@ -464,6 +464,18 @@ def run_ours(args):
                           "preparation, each alone as a graph replay; the timed steps "
                           "overlap the two on two streams"}
         del g_on, g_deal
+        # Per-kernel busy time of the online phase alone (eager, instrumented):
+        # what of the step's kernel time sits on the online critical path.
+        mpc.profile_reset()
+        mpc.profile_enable(True)
+        for _ in range(3):
+            flush.zero_()
+            net.reveal(net.online(x_dev, sch, 0, wait_dealer=False))
+        torch.cuda.synchronize()
+        mpc.profile_enable(False)
+        phases["online_kernel_busy_ms"] = {
+            k: mpc.profile_busy(k) / 3 for k in ("gemm_limb", "limb_planes", "private_relu_fused")
+            if mpc.profile_read(k)[0]}
         # The same with the convolutions' input-independent half left in the
         # online phase (no prepared planes): the split the timed steps do not use.
         was_prepared = net.prepared
