@@ -44,6 +44,8 @@ LIMB_GEMM_PLANE_BYTES_PER_LAUNCH = 87.3e6
 # ncu sm__pipe_tensor_cycles_active (% of elapsed cycles) of the same kernel in
 # one capture each: an online speech-layer launch, and the 4096^3 ring GEMM.
 LIMB_GEMM_TENSOR_ACTIVE_SPEECH = 64.4
+# ... and time-weighted over the nine limb GEMM launches of one speech forward.
+LIMB_GEMM_TENSOR_ACTIVE_SPEECH_STEP = 59.7
 LIMB_GEMM_TENSOR_ACTIVE_4096 = 80.7
 REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
 
@@ -538,6 +540,7 @@ def run_ours(args):
                 "ncu_tensor_active_pct": LIMB_GEMM_TENSOR_ACTIVE_SPEECH,
                 "ncu_tensor_active_note": "sm__pipe_tensor_cycles_active of an online "
                                           "speech-layer launch, one ncu capture (serialised)",
+                "ncu_tensor_active_step_pct": LIMB_GEMM_TENSOR_ACTIVE_SPEECH_STEP,
                 "peak_source": peak_src + " (bf16 burst)",
                 "launches_per_step": launches / args.steps,
                 "busy_ms_per_step": kms / args.steps,
