@@ -202,17 +202,21 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
                           uint64_t* A, uint64_t* B, uint64_t* C, int algo, void* ws,
                           size_t ws_bytes, void* stream);
 
-/* A batch of `count` (1 <= count <= MPC_MAX_TRIPLE_BATCH) convolution triples
- * of one descriptor d, triple j dealt at op id op_ids[j] into the caller's
+/* A batch of `count` (1 <= count <= MPC_MAX_TRIPLE_BATCH) convolution triples,
+ * triple j of descriptor d[j] dealt at op id op_ids[j] into the caller's
  * A[j], B[j], C[j] (device, shaped as for mpc_ttp_conv2d_triple): word for
  * word what `count` calls of mpc_ttp_conv2d_triple give (the dealer's role
- * in the paper's offline phase, §4).  On the limb engine the count
- * products c_j = conv(a_j, b_j) run as the jobs of one GEMM launch after one
- * digit-plane launch; on the plain engine the triples are dealt in turn.
- * op_ids, A, B and C are host arrays of count entries.  ws: device workspace
- * of mpc_conv2d_triples_workspace_size() bytes (0 for invalid arguments).
- * Errors: MPC_EINVAL (party count, count, descriptor, null pointers),
- * MPC_ENOMEM (workspace), MPC_EUNSUPPORTED (shape outside the limb engine). */
+ * in the paper's offline phase, §4).  Every d[j] must have d[0]'s output
+ * shape (c_out, batch, ho, wo); c_in, h, w, the kernel, stride and padding
+ * may differ.  On the limb engine the count products c_j = conv(a_j, b_j)
+ * run as the jobs of one GEMM launch (each with its own K, split alike)
+ * after one digit-plane launch per run of equal descriptors; on the plain
+ * engine the triples are dealt in turn.  d, op_ids, A, B and C are host
+ * arrays of count entries.  ws: device workspace of
+ * mpc_conv2d_triples_workspace_size() bytes (0 for invalid arguments).
+ * Errors: MPC_EINVAL (party count, count, a descriptor, output shapes that
+ * differ, null pointers), MPC_ENOMEM (workspace), MPC_EUNSUPPORTED (shape
+ * outside the limb engine). */
 #define MPC_MAX_TRIPLE_BATCH 8
 size_t mpc_conv2d_triples_workspace_size(int P, int count, const mpc_conv_desc* d, int algo);
 int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t seed,

@@ -177,26 +177,38 @@ def ttp_conv2d_triple(P, d, seed, op_id, algo=PLAIN, device="cuda", out=None, ws
     return A, B, C
 
 
+def _desc_array(d, count):
+    descs = [d] * count if isinstance(d, _lib.ConvDesc) else list(d)
+    if len(descs) != count:
+        raise ValueError(f"{len(descs)} descriptors for {count} triples")
+    return (_lib.ConvDesc * count)(*descs), descs
+
+
 def conv2d_triples_workspace_size(P, count, d, algo=PLAIN):
-    return int(_L().mpc_conv2d_triples_workspace_size(P, count, ctypes.byref(d), algo))
+    """d: one descriptor for all `count` triples, or a list of count."""
+    arr, _ = _desc_array(d, count)
+    return int(_L().mpc_conv2d_triples_workspace_size(P, count, arr, algo))
 
 
 def ttp_conv2d_triples(P, d, seed, op_ids, algo=PLAIN, device="cuda", outs=None, ws=None):
-    """Convolution triples of one descriptor at each op id in `op_ids`
-    (mpc_ttp_conv2d_triples); outs: one (A, B, C) per op id, or None."""
+    """Convolution triples at each op id in `op_ids` (mpc_ttp_conv2d_triples):
+    d is one descriptor for all of them or a list with one per op id (one
+    output shape); outs: one (A, B, C) per op id, or None."""
     count = len(op_ids)
-    ho, wo = conv_out_hw(d)
+    arr, descs = _desc_array(d, count)
     if outs is None:
-        outs = [(_words((P, d.batch, d.c_in, d.h, d.w), device),
-                 _words((P, d.c_out, d.c_in, d.kh, d.kw), device),
-                 _words((P, d.batch, d.c_out, ho, wo), device)) for _ in range(count)]
-    need = conv2d_triples_workspace_size(P, count, d, algo)
+        outs = []
+        for dj in descs:
+            ho, wo = conv_out_hw(dj)
+            outs.append((_words((P, dj.batch, dj.c_in, dj.h, dj.w), device),
+                         _words((P, dj.c_out, dj.c_in, dj.kh, dj.kw), device),
+                         _words((P, dj.batch, dj.c_out, ho, wo), device)))
+    need = _L().mpc_conv2d_triples_workspace_size(P, count, arr, algo)
     ws = _ws(need, device) if ws is None else ws
     ids = (ctypes.c_uint64 * count)(*op_ids)
     ptrs = [(ctypes.c_void_p * count)(*[_ptr(t[i]) for t in outs]) for i in range(3)]
-    _check(_L().mpc_ttp_conv2d_triples(P, count, ctypes.byref(d), seed, ids, ptrs[0], ptrs[1],
-                                       ptrs[2], algo, _ptr(ws, "ws", torch.uint8), ws.numel(),
-                                       _stream()))
+    _check(_L().mpc_ttp_conv2d_triples(P, count, arr, seed, ids, ptrs[0], ptrs[1], ptrs[2], algo,
+                                       _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
     return outs
 
 

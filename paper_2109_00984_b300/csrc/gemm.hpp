@@ -49,10 +49,14 @@ struct GemmArgs {
   int defer_reduce;
   u64* partial;
   const ConvGather* gather;  // host pointer; when set, B1/B2 are implicit im2col (limb only)
-  // With gather and one operand pair: job j's B1 is gathered from
-  // gather->src2[j] (no opening), one gather per job, instead of every job
-  // sharing the opened gather (the dealer's products of a batch of triples).
+  // With gather and one operand pair: `gather` points to njobs convolutions,
+  // job j's B1 gathered from gather[j].src2[0] (no opening) and its K =
+  // c_in kh kw of gather[j].d (at most K; M and N are every job's), instead of
+  // every job sharing the opened gather (the dealer's products of a batch of
+  // triples).
   int gather_per_job;
+  // At most this many splits (0: no cap), e.g. the shortest per-job K's sub-steps.
+  int max_splits;
   // Limb engine, convolution with gather only: digit planes cut ahead of the
   // call by limb_conv_prepare (layout in its comment).  The A operands and
   // every job's B2 are taken from there; only the opened gather B1 is cut in

@@ -132,6 +132,9 @@ struct LimbParams {
   i64 M, N, hw_out;
   int T;   // K sub-steps of 16 over both pairs
   int T1;  // sub-steps of one pair
+  // One-pair jobs of different K (a batch of dealer products): job j's
+  // sub-steps when Tj[j] > 0, else T (= T1).
+  int Tj[MPC_MAX_PARTIES];
   int trunc_bits;
   int splits, njobs;
   int* status;
@@ -302,7 +305,7 @@ __device__ __forceinline__ void producer_loop(const LimbParams& p, int job, int 
                                               volatile int* abort_flag) {
   const CUtensorMap* ta[2] = {&p.tmA[0][job], &p.tmA[1][job]};
   const CUtensorMap* tb[2] = {&p.tmB[0][job], &p.tmB[1][job]};
-  const int T1 = p.T1;
+  const int T1 = p.Tj[job] > 0 ? p.Tj[job] : p.T1;
   int st = 0, n = 0;
   uint32_t ph = 0;
   // One box of digit planes (plane group h: 0..3 or 4..7) of sub-step t of A
@@ -430,8 +433,9 @@ __global__ void __launch_bounds__(kThreads, 1) limb_gemm_kernel(const __grid_con
   const int job = blockIdx.z / p.splits, split = blockIdx.z % p.splits;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   // This CTA's K sub-steps [t_begin, t_end), run once per pass.
-  const int t_begin = (int)((i64)p.T * split / p.splits);
-  const int t_end = (int)((i64)p.T * (split + 1) / p.splits);
+  const int T = p.Tj[job] > 0 ? p.Tj[job] : p.T;
+  const int t_begin = (int)((i64)T * split / p.splits);
+  const int t_end = (int)((i64)T * (split + 1) / p.splits);
   const uint32_t sbase = (smem_u32(dsmem) + 1023u) & ~1023u;
 
   if (threadIdx.x == 0) {
@@ -1549,7 +1553,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
         return rc;
     }
   }
-  for (int pr = 0; pr < npairs && !prep; ++pr) {
+  for (int pr = 0; pr < npairs && !prep && !per_job; ++pr) {
     for (int j = 0; j < g.njobs; ++j) {
       const u64* src = pr ? g.jobs[j].A2 : g.jobs[j].A1;
       int hit = -1;
@@ -1563,15 +1567,49 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
       if (int rc = encode_planes(&prm.tmA[pr][j], ja.j[hit].out, g.M, K1p, BM)) return rc;
     }
   }
-  int z0 = 0;  // first gather output cut by this call
   if (per_job) {
-    // gather outputs 1 .. njobs: job j's B1 from src2[j]
-    z0 = 1;
-    nb = g.njobs;
-    for (int j = 0; j < g.njobs; ++j) {
-      jbv.j[1 + j] = PlaneJob{nullptr, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
-      w += b_bytes;
-      if (int rc = encode_planes(&prm.tmB[0][j], jbv.j[1 + j].out, g.N, K1p, BN)) return rc;
+    // Job j is its own convolution g.gather[j] (same M and N for all jobs, K_j
+    // <= g.K): planes A_j (M x K_j) of jobs[j].A1 and B_j (N x K_j) gathered
+    // from g.gather[j].src2[0], its own sub-step count Tj[j]; one plane launch
+    // per run of jobs with one descriptor.
+    KernelTimer timer("limb_planes", s);
+    for (int j0 = 0; j0 < g.njobs;) {
+      const ConvGather& c0 = g.gather[j0];
+      int j1 = j0 + 1;
+      while (j1 < g.njobs && memcmp(&g.gather[j1].d, &c0.d, sizeof(c0.d)) == 0) ++j1;
+      const i64 Kj = c0.d.c_in * c0.d.kh * c0.d.kw, Kjp = pair_k(Kj);
+      const i64 data = c0.d.batch * c0.d.c_in * c0.d.h * c0.d.w;
+      if (Kj < 1 || Kj > g.K || data >= (1ll << 31) || (i64)8 * g.N * Kjp >= (1ll << 62))
+        return fail(MPC_EUNSUPPORTED, "per-job convolution outside the limb gather");
+      if (Kjp / KS < g.splits) return fail(MPC_EUNSUPPORTED, "per-job K shorter than its splits");
+      PlanesLaunch pl;
+      memset(&pl, 0, sizeof(pl));
+      pl.cg = c0;
+      pl.M = g.M;
+      pl.N = g.N;
+      pl.K = Kj;
+      pl.Kp = Kjp;
+      pl.na = pl.nb = j1 - j0;
+      pl.z0 = 1;
+      for (int j = j0; j < j1; ++j) {
+        const int i = j - j0;
+        pl.ja.j[i] = PlaneJob{g.jobs[j].A1, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+        if (int rc = encode_planes(&prm.tmA[0][j], w, g.M, Kjp, BM)) return rc;
+        w += al256((size_t)16 * g.M * Kjp);
+        pl.jb.j[1 + i] = PlaneJob{nullptr, nullptr, reinterpret_cast<__nv_bfloat16*>(w)};
+        if (int rc = encode_planes(&prm.tmB[0][j], w, g.N, Kjp, BN)) return rc;
+        w += al256((size_t)16 * g.N * Kjp);
+        pl.cg.src2[i] = g.gather[j].src2[0];
+        prm.Tj[j] = (int)(Kjp / KS);
+      }
+      pl.bx = (int)ceil_div(Kjp / KS, 8);
+      pl.by = (int)ceil_div(g.N, 16);
+      pl.a_blk = (int)std::min<i64>(ceil_div(g.M * (Kjp / 8), 256), 148 * 4);
+      const i64 blocks = (i64)pl.na * pl.a_blk + (i64)pl.nb * pl.bx * pl.by;
+      if (blocks > 0x7FFFFFFFll) return fail(MPC_EUNSUPPORTED, "plane pass grid too large");
+      limb_planes<true><<<(unsigned)blocks, 256, 0, s>>>(pl);
+      if (int rc = check_launch("limb_planes")) return rc;
+      j0 = j1;
     }
   } else if (g.gather) {
     // pair 1: the opened gather, shared; pair 2 (two-pair products): one per job
@@ -1609,7 +1647,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     prm.C[j] = g.jobs[j].C;
     prm.Z[j] = g.jobs[j].Z;
   }
-  {
+  if (!per_job) {
     KernelTimer timer("limb_planes", s);
     PlanesLaunch pl;
     memset(&pl, 0, sizeof(pl));
@@ -1621,7 +1659,6 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     pl.Kp = K1p;
     pl.na = na;
     pl.nb = nb;
-    pl.z0 = z0;
     pl.bx = (int)ceil_div(K1p / KS, 8);  // B side: blocks of 8 sub-steps x 16 columns
     pl.by = (int)ceil_div(g.N, 16);
     // A side: about as many threads as 8-k groups, at most 4 blocks per SM and job.

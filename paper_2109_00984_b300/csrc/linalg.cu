@@ -378,6 +378,7 @@ int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s, Ge
   if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
   const int npairs = g.jobs[0].A2 ? 2 : 1;
   g.splits = engine_splits(algo, g.M, g.N, g.K, npairs, g.njobs);
+  if (g.max_splits > 0 && g.splits > g.max_splits) g.splits = g.max_splits;
   const size_t pb = align256(partial_bytes(g.splits, g.njobs, g.M, g.N));
   if (ws_bytes < pb) return fail(MPC_ENOMEM, "engine workspace too small for split-K partials");
   g.partial = g.splits > 1 ? static_cast<u64*>(ws) : nullptr;
@@ -821,21 +822,54 @@ int mpc_ttp_conv2d_triple(int P, const mpc_conv_desc* d, uint64_t seed, uint64_t
   return share_product(P, used, seed, op_id, (u64*)C, s);
 }
 
-// A batch of `count` convolution triples of one shape.  On the limb engine
-// the count products c_j = conv(a_j, b_j) run as the jobs of one GEMM launch
-// (one digit-plane launch gathers every a_j); on the plain engine the
+// A batch of `count` convolution triples with one output shape (c_out, batch,
+// ho, wo).  On the limb engine the count products c_j = conv(a_j, b_j) run
+// as the jobs of one GEMM launch, each with its own K (one digit-plane launch
+// per run of equal descriptors gathers the a_j); on the plain engine the
 // triples are dealt one by one.
+namespace {
+
+struct TripleBatch {
+  i64 M, N, ho, wo, Kmax;
+};
+
+int check_triple_batch(int count, const mpc_conv_desc* d, TripleBatch* b) {
+  MPC_REQUIRE(d != nullptr, "null descriptor array");
+  i64 ho0, wo0;
+  if (int rc = validate_conv(&d[0], &ho0, &wo0)) return rc;
+  b->M = d[0].c_out;
+  b->N = d[0].batch * ho0 * wo0;
+  b->ho = ho0;
+  b->wo = wo0;
+  b->Kmax = 0;
+  for (int j = 0; j < count; ++j) {
+    i64 ho, wo;
+    if (int rc = validate_conv(&d[j], &ho, &wo)) return rc;
+    MPC_REQUIRE(d[j].c_out == d[0].c_out && d[j].batch == d[0].batch && ho == ho0 && wo == wo0,
+                "triple %d: output shape differs from triple 0's", j);
+    b->Kmax = std::max<i64>(b->Kmax, d[j].c_in * d[j].kh * d[j].kw);
+  }
+  return MPC_OK;
+}
+
+}  // namespace
+
 size_t mpc_conv2d_triples_workspace_size(int P, int count, const mpc_conv_desc* d, int algo) {
-  i64 ho, wo;
+  TripleBatch tb;
   if (P < 1 || P > MPC_MAX_PARTIES || count < 1 || count > MPC_MAX_TRIPLE_BATCH ||
-      validate_conv(d, &ho, &wo) != MPC_OK)
+      check_algo(algo) != MPC_OK || check_triple_batch(count, d, &tb) != MPC_OK)
     return 0;
-  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
-  const i64 nx = d->batch * d->c_in * d->h * d->w;
-  algo = resolve_algo(algo, M, N, K);
-  if (algo != MPC_ALGO_LIMB || !limb_supported(M, N, K)) return conv_triple_ws(*d, ho, wo, algo);
-  return (size_t)count * (align256(words(nx)) + align256(words(M * K))) +
-         engine_ws(MPC_ALGO_LIMB, M, N, K, 1, count);
+  algo = resolve_algo(algo, tb.M, tb.N, tb.Kmax);
+  if (algo != MPC_ALGO_LIMB || !limb_supported(tb.M, tb.N, tb.Kmax) || count == 1) {
+    size_t need = 0;
+    for (int j = 0; j < count; ++j) need = std::max(need, conv_triple_ws(d[j], tb.ho, tb.wo, algo));
+    return need;
+  }
+  size_t need = engine_ws(MPC_ALGO_LIMB, tb.M, tb.N, tb.Kmax, 1, count);
+  for (int j = 0; j < count; ++j)
+    need += align256(words(d[j].batch * d[j].c_in * d[j].h * d[j].w)) +
+            align256(words(tb.M * d[j].c_in * d[j].kh * d[j].kw));
+  return need;
 }
 
 int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t seed,
@@ -846,40 +880,37 @@ int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t se
   if (int rc = check_algo(algo)) return rc;
   MPC_REQUIRE(count >= 1 && count <= MPC_MAX_TRIPLE_BATCH, "count %d outside [1, %d]", count,
               MPC_MAX_TRIPLE_BATCH);
-  i64 ho, wo;
-  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  TripleBatch tb;
+  if (int rc = check_triple_batch(count, d, &tb)) return rc;
   MPC_REQUIRE(op_ids && A && B && C, "null pointer");
   for (int j = 0; j < count; ++j) MPC_REQUIRE(A[j] && B[j] && C[j], "null pointer (triple %d)", j);
-  const i64 M = d->c_out, K = d->c_in * d->kh * d->kw, N = d->batch * ho * wo;
-  const i64 nx = d->batch * d->c_in * d->h * d->w;
-  algo = resolve_algo(algo, M, N, K);
+  const i64 M = tb.M, N = tb.N;
+  algo = resolve_algo(algo, M, N, tb.Kmax);
   if (algo != MPC_ALGO_LIMB || count == 1) {
     for (int j = 0; j < count; ++j)
-      if (int rc = mpc_ttp_conv2d_triple(P, d, seed, op_ids[j], A[j], B[j], C[j], algo, ws,
+      if (int rc = mpc_ttp_conv2d_triple(P, &d[j], seed, op_ids[j], A[j], B[j], C[j], algo, ws,
                                          ws_bytes, stream))
         return rc;
     return MPC_OK;
   }
-  if (!limb_supported(M, N, K))
+  if (!limb_supported(M, N, tb.Kmax))
     return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
   const size_t need = mpc_conv2d_triples_workspace_size(P, count, d, algo);
   MPC_REQUIRE(ws != nullptr, "null workspace");
   if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
   cudaStream_t s = as_stream(stream);
   Carve cv(ws);
-  ConvGather cg{};
-  cg.d = *d;
-  cg.ho = ho;
-  cg.wo = wo;
+  ConvGather cg[MPC_MAX_TRIPLE_BATCH] = {};
   GemmArgs g{};
   g.M = M;
   g.N = N;
-  g.K = K;
-  g.hw_out = ho * wo;
+  g.K = tb.Kmax;
+  g.hw_out = tb.ho * tb.wo;
   g.njobs = count;
-  g.gather = &cg;
+  g.gather = cg;
   g.gather_per_job = 1;
   g.defer_reduce = 1;  // the correction kernels add the split-K partial sums themselves
+  g.max_splits = 64;
   // The fills, one launch each: a single launch for all of them made the dealer
   // alone 7 % faster but the overlapped speech step 1 % slower (one wide
   // launch takes every SM from the online phase at once; small ones fit in
@@ -890,6 +921,8 @@ int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t se
   u64 fop[2 * MPC_MAX_TRIPLE_BATCH];
   unsigned frole[2 * MPC_MAX_TRIPLE_BATCH];
   for (int j = 0; j < count; ++j) {
+    const i64 nx = d[j].batch * d[j].c_in * d[j].h * d[j].w;
+    const i64 K = d[j].c_in * d[j].kh * d[j].kw;
     u64* a = cv.take(nx);
     u64* b = cv.take(M * K);
     fout[2 * j] = (u64*)A[j];
@@ -901,8 +934,13 @@ int mpc_ttp_conv2d_triples(int P, int count, const mpc_conv_desc* d, uint64_t se
     fn[2 * j + 1] = M * K;
     frole[2 * j + 1] = MPC_ROLE_TRIPLE_B;
     fop[2 * j] = fop[2 * j + 1] = op_ids[j];
-    cg.src2[j] = a;
+    cg[j].d = d[j];
+    cg[j].ho = tb.ho;
+    cg[j].wo = tb.wo;
+    cg[j].src2[0] = a;
     g.jobs[j] = GemmJob{b, nullptr, nullptr, nullptr, nullptr, (u64*)C[j] + (i64)(P - 1) * M * N};
+    // every job's K range is split the same number of ways: at most its sub-steps
+    g.max_splits = std::min<int>(g.max_splits, (int)ceil_div(K, 16));
   }
   for (int q = 0; q < 2 * count; ++q)
     if (int rc = launch_fill_sum(P, fn[q], seed, fop[q], frole[q], fout[q], fsum[q], s)) return rc;

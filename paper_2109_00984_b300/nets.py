@@ -28,8 +28,9 @@ import torch
 from . import api
 
 
-def _same_desc(a, b):
-    return all(getattr(a, f) == getattr(b, f) for f, _ in a._fields_)
+def _same_output(a, b):
+    """Convolutions whose triples one batched dealer call can deal together."""
+    return (a.c_out, a.batch) == (b.c_out, b.batch) and api.conv_out_hw(a) == api.conv_out_hw(b)
 
 
 class PrivateConv1dStack:
@@ -38,8 +39,8 @@ class PrivateConv1dStack:
                  prepare_weights=False, batch_triples=True):
         self.P = 2
         self.fused_relu = fused_relu
-        # deal the triples of consecutive same-shaped layers in one batched call
-        # (one GEMM launch for all their products on the limb engine)
+        # deal the triples of consecutive layers with one output shape in one
+        # batched call (one GEMM launch for all their products on the limb engine)
         self.batch_triples = batch_triples
         self.overlap_dealer = overlap_dealer
         self.algo = algo
@@ -94,18 +95,18 @@ class PrivateConv1dStack:
             C=torch.empty((P, d.batch, d.c_out) + tuple(api.conv_out_hw(d)), dtype=torch.int64,
                           device=dev)) for d in self.descs] for _ in range(2)]
         self.ready = [[None] * len(self.descs) for _ in range(2)]
-        # runs of consecutive layers with one descriptor: (first layer, count)
+        # runs of consecutive layers with one output shape: (first layer, count)
         self.deal_groups = []
         for l, d in enumerate(self.descs):
             g = self.deal_groups[-1] if self.deal_groups else None
             if (self.batch_triples and g is not None and g[1] < api.MAX_TRIPLE_BATCH and
-                    _same_desc(self.descs[g[0]], d)):
+                    _same_output(self.descs[g[0]], d)):
                 self.deal_groups[-1] = (g[0], g[1] + 1)
             else:
                 self.deal_groups.append((l, 1))
         for first, count in self.deal_groups:
-            ws_bytes = max(ws_bytes, api.conv2d_triples_workspace_size(P, count, self.descs[first],
-                                                                      self.algo))
+            ws_bytes = max(ws_bytes, api.conv2d_triples_workspace_size(
+                P, count, self.descs[first:first + count], self.algo))
         self.prepared = False
         self.prep = None
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -157,8 +158,8 @@ class PrivateConv1dStack:
                     api.ttp_conv2d_triple(self.P, self.descs[first], seed, ops[0], self.algo,
                                           out=outs[0], ws=ws)
                 else:
-                    api.ttp_conv2d_triples(self.P, self.descs[first], seed, ops, self.algo,
-                                           outs=outs, ws=ws)
+                    api.ttp_conv2d_triples(self.P, self.descs[first:first + count], seed, ops,
+                                           self.algo, outs=outs, ws=ws)
                 for l in layers:
                     t = self.trip[slot][l]
                     if self.prepared:

@@ -75,25 +75,25 @@ class PrivateResNet18:
         triples = {}
         N, _, H, W = x_shape
         C = 3
-        pending = []   # (key, desc) of consecutive same-shaped convolutions
+        pending = []   # (key, desc) of consecutive convolutions with one output shape
 
         def flush():
             if not pending:
                 return
-            d = pending[0][1]
+            descs = [dd for _, dd in pending]
             keys = [k for k, _ in pending]
             if len(keys) == 1:
-                ws = self._dealer_ws(api.conv2d_triple_workspace_size(self.P, d, self.algo))
-                got = [self._deal_conv(d, ops[keys[0]], ws)]
+                ws = self._dealer_ws(api.conv2d_triple_workspace_size(self.P, descs[0], self.algo))
+                got = [self._deal_conv(descs[0], ops[keys[0]], ws)]
             else:
-                ws = self._dealer_ws(api.conv2d_triples_workspace_size(self.P, len(keys), d,
+                ws = self._dealer_ws(api.conv2d_triples_workspace_size(self.P, len(keys), descs,
                                                                        self.algo))
-                got = api.ttp_conv2d_triples(self.P, d, self.seed, [ops[k] for k in keys],
+                got = api.ttp_conv2d_triples(self.P, descs, self.seed, [ops[k] for k in keys],
                                              self.algo, device=self.device, ws=ws)
-            for k, t in zip(keys, got):
+            for k, dd, t in zip(keys, descs, got):
                 triples[k] = t
-                if self.prepare and api.conv2d_prep_size(self.P, d) > 0:
-                    triples[k + "#prep"] = api.beaver_conv2d_prepare(self.W[k], t[0], t[1], d)
+                if self.prepare and api.conv2d_prep_size(self.P, dd) > 0:
+                    triples[k + "#prep"] = api.beaver_conv2d_prepare(self.W[k], t[0], t[1], dd)
             ev = torch.cuda.Event()
             ev.record(torch.cuda.current_stream())
             for k in keys:
@@ -102,9 +102,10 @@ class PrivateResNet18:
 
         def conv(name, cin, cout, k, stride, pad, h, w, key):
             d = api.conv_desc(N, cin, h, w, cout, k, k, stride, stride, pad, pad)
+            d0 = pending[0][1] if pending else None
             if pending and (len(pending) == api.MAX_TRIPLE_BATCH or
-                            not all(getattr(d, f) == getattr(pending[0][1], f)
-                                    for f, _ in d._fields_)):
+                            (d.c_out, d.batch) != (d0.c_out, d0.batch) or
+                            api.conv_out_hw(d) != api.conv_out_hw(d0)):
                 flush()
             pending.append((key, d))
             return api.conv_out_hw(d)

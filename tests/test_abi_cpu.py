@@ -170,25 +170,33 @@ def test_prepared_conv_validation(lib):
 def test_conv_triples_batch_validation(lib):
     from paper_2109_00984_b300 import _lib
     d = _lib.ConvDesc(1, 64, 1, 100, 40, 1, 7, 1, 1, 0, 3)
-    dp = ctypes.byref(d)
-    one = lib.mpc_conv2d_triple_workspace_size(2, dp, 1)
-    three = lib.mpc_conv2d_triples_workspace_size(2, 3, dp, 1)
+    # same output shape (40 x 100), other input channels, kernel, stride, padding
+    d2 = _lib.ConvDesc(1, 32, 1, 200, 40, 1, 11, 1, 2, 0, 5)
+    other = _lib.ConvDesc(1, 64, 1, 100, 48, 1, 7, 1, 1, 0, 3)   # other c_out
+    arr = (_lib.ConvDesc * 9)(*([d] * 9))
+    one = lib.mpc_conv2d_triple_workspace_size(2, ctypes.byref(d), 1)
+    three = lib.mpc_conv2d_triples_workspace_size(2, 3, arr, 1)
     assert 0 < one < three
-    assert lib.mpc_conv2d_triples_workspace_size(2, 1, dp, 1) == one
+    assert lib.mpc_conv2d_triples_workspace_size(2, 1, arr, 1) == one
     # the plain engine deals the triples in turn in one triple's workspace
-    assert lib.mpc_conv2d_triples_workspace_size(2, 3, dp, 0) == \
-        lib.mpc_conv2d_triple_workspace_size(2, dp, 0)
+    assert lib.mpc_conv2d_triples_workspace_size(2, 3, arr, 0) == \
+        lib.mpc_conv2d_triple_workspace_size(2, ctypes.byref(d), 0)
     for bad in (0, 9):
-        assert lib.mpc_conv2d_triples_workspace_size(2, bad, dp, 1) == 0
+        assert lib.mpc_conv2d_triples_workspace_size(2, bad, arr, 1) == 0
+    mixed = (_lib.ConvDesc * 3)(d, d2, d)
+    assert 0 < lib.mpc_conv2d_triples_workspace_size(2, 3, mixed, 1) < three   # d2's K is smaller
+    assert lib.mpc_conv2d_triples_workspace_size(2, 3, (_lib.ConvDesc * 3)(d, other, d), 1) == 0
     ids = (ctypes.c_uint64 * 3)(1, 2, 3)
     ptrs = (ctypes.c_void_p * 3)(0x1000, 0x1000, 0x1000)
     holes = (ctypes.c_void_p * 3)(0x1000, None, 0x1000)
 
-    def call(count, op_ids=ids, A=ptrs, ws_bytes=three):
-        return lib.mpc_ttp_conv2d_triples(2, count, dp, 1, op_ids, A, ptrs, ptrs, 1, FAKE,
+    def call(count, descs=arr, op_ids=ids, A=ptrs, ws_bytes=three):
+        return lib.mpc_ttp_conv2d_triples(2, count, descs, 1, op_ids, A, ptrs, ptrs, 1, FAKE,
                                           ws_bytes, NULL)
     assert call(0) == E["EINVAL"]
     assert call(9) == E["EINVAL"]
     assert call(3, op_ids=None) == E["EINVAL"]
     assert call(3, A=holes) == E["EINVAL"]
+    assert call(3, descs=(_lib.ConvDesc * 3)(d, other, d)) == E["EINVAL"]
+    assert call(3, descs=None) == E["EINVAL"]
     assert call(3, ws_bytes=three - 1) == E["ENOMEM"]

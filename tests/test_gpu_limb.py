@@ -162,6 +162,41 @@ def test_conv_triples_batch_matches_oracle(mpc, P, engine, geom):
         assert np.array_equal(host(gC), rC)
 
 
+@pytest.mark.parametrize("P", [2, 3])
+def test_conv_triples_mixed_descriptors(mpc, P):
+    """One batch of triples for convolutions that differ in input channels,
+    kernel, stride and padding but share the output shape (c_out 40, 64
+    columns): each product has its own K (one GEMM launch, one plane launch per
+    run of equal descriptors), the splits capped by the shortest K (a 1 x 1
+    convolution of 16 channels: one sub-step)."""
+    geoms = [
+        # (batch, c_in, h, w, c_out, kh, kw, stride, pad_h, pad_w)
+        (1, 160, 1, 64, 40, 1, 7, 1, 0, 3),
+        (1, 160, 1, 64, 40, 1, 7, 1, 0, 3),
+        (1, 48, 1, 128, 40, 1, 11, 2, 0, 5),
+        (1, 16, 1, 64, 40, 1, 1, 1, 0, 0),
+    ]
+    descs = [mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+             for b, ci, h, w, co, kh, kw, st, ph, pw in geoms]
+    ops = [700, 711, 722, 733]
+    outs = mpc.ttp_conv2d_triples(P, descs, SEED, ops, algo=mpc.LIMB)
+    mpc.sync_status()
+    for g, op, (gA, gB, gC) in zip(geoms, ops, outs):
+        b, ci, h, w, co, kh, kw, st, ph, pw = g
+        rA, rB, rC = dealer.conv2d_triple(P, (b, ci, h, w), (co, ci, kh, kw), st, ph, SEED, op,
+                                          pad_w=pw)
+        assert np.array_equal(host(gA), rA) and np.array_equal(host(gB), rB)
+        assert np.array_equal(host(gC), rC)
+    # without the 1 x 1 convolution the batch is split along K
+    outs = mpc.ttp_conv2d_triples(P, descs[:3], SEED, ops[:3], algo=mpc.LIMB)
+    mpc.sync_status()
+    for g, op, (gA, gB, gC) in zip(geoms, ops, outs):
+        b, ci, h, w, co, kh, kw, st, ph, pw = g
+        _, _, rC = dealer.conv2d_triple(P, (b, ci, h, w), (co, ci, kh, kw), st, ph, SEED, op,
+                                        pad_w=pw)
+        assert np.array_equal(host(gC), rC)
+
+
 @pytest.mark.parametrize("P,count", [(8, 2), (2, 8)])
 def test_conv_triples_batch_edges(mpc, P, count):
     """Eight parties, and the largest batch, on a tiny convolution (N = 15 output
