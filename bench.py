@@ -33,19 +33,19 @@ WORKLOAD = ("speech-shaped private conv stack: 2 parties, batch 1, input 80x1600
             "Conv1d 80->256 k11 s2 + 6x Conv1d 256->256 k7 (pad k//2), each Beaver conv + "
             "truncation 2^16 + private ReLU (A2B/Kogge-Stone/B2A), Z/2^64, dealer in the step")
 L2_FLUSH_BYTES = 256 << 20
-# DRAM traffic of the limb GEMM per launch, averaged over the 9 launches of one
-# speech step (7 online GEMMs of two pairs for two parties; the dealer's layer-1
-# GEMM of one operand pair, and one launch for the six same-shaped layers'
-# products), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# on the current kernel; and the digit-plane bytes those launches must read
-# (785.5 MB per step: 16 bytes per operand word).
-LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 97.4e6
-LIMB_GEMM_PLANE_BYTES_PER_LAUNCH = 87.3e6
+# DRAM traffic of the limb GEMM per launch, averaged over the 8 launches of one
+# speech step (7 online GEMMs of two pairs for two parties, and one launch for
+# the dealer's seven one-pair products), from an ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum on the current kernel; and the
+# digit-plane bytes those launches must read (785.5 MB per step: 16 bytes per
+# operand word).
+LIMB_GEMM_DRAM_BYTES_PER_LAUNCH = 110.9e6
+LIMB_GEMM_PLANE_BYTES_PER_LAUNCH = 98.2e6
 # ncu sm__pipe_tensor_cycles_active (% of elapsed cycles) of the same kernel in
 # one capture each: an online speech-layer launch, and the 4096^3 ring GEMM.
 LIMB_GEMM_TENSOR_ACTIVE_SPEECH = 64.4
-# ... and time-weighted over the nine limb GEMM launches of one speech forward.
-LIMB_GEMM_TENSOR_ACTIVE_SPEECH_STEP = 59.7
+# ... and time-weighted over the eight limb GEMM launches of one speech forward.
+LIMB_GEMM_TENSOR_ACTIVE_SPEECH_STEP = 62.6
 LIMB_GEMM_TENSOR_ACTIVE_4096 = 80.7
 REF_FRAMES = 160          # oracle sample: the whole stack on 1/10 of the frames
 
@@ -533,7 +533,7 @@ def run_ours(args):
         roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": bf16_peak,
                 "unit": "TFLOP/s", "frac": achieved / bf16_peak,
                 "traffic": LIMB_GEMM_DRAM_BYTES_PER_LAUNCH,
-                "traffic_note": "bytes per launch, mean of the 9 limb GEMM launches of one "
+                "traffic_note": "bytes per launch, mean of the 8 limb GEMM launches of one "
                                 "step (dram__bytes_read.sum + dram__bytes_write.sum, ncu); "
                                 "the digit planes they read are "
                                 f"{LIMB_GEMM_PLANE_BYTES_PER_LAUNCH / 1e6:.1f} MB per launch",
