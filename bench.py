@@ -562,7 +562,7 @@ def run_ours(args):
         extras["gemm_sweep"] = extra_gemm_sweep(dev, peaks)
         extras["hbm_kernels"] = extra_hbm_kernels(dev, peaks, [1 << 26])
         extras["resnet18"] = extra_resnet(dev, peaks, steps=3, warmup=1)
-        extras["batched"] = extra_batched(dev, reps=3)
+        extras["batched"] = extra_batched(dev, reps=5)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # host baseline: rank 0 at N = 1 only
