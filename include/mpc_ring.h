@@ -521,6 +521,16 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
 int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
                            uint64_t op_id, void* stream);
 
+/* mpc_private_relu_fused of X + S (§5.2 "Private addition" then the ReLU): the
+ * same words as mpc_add(2, n, X, 0, S, 0, T, 0) followed by
+ * mpc_private_relu_fused(2, n, T, Y, seed, op_id), with the local addition
+ * folded into the ReLU
+ * kernel's load (a residual connection's sum goes straight into its ReLU).
+ * S device u64 [2][n] or null (then exactly mpc_private_relu_fused); Y may
+ * alias X or S.  Errors as mpc_private_relu_fused. */
+int mpc_private_relu_fused_add(int P, int64_t n, const uint64_t* X, const uint64_t* S,
+                               uint64_t* Y, uint64_t seed, uint64_t op_id, void* stream);
+
 /* ---- function approximations (App. D.2), two parties, fused dealer -------- */
 /* Each call below evaluates one function elementwise on two-party shares of
  * fixed-point values (2^16) in ONE launch per element range: every dealer

@@ -525,12 +525,19 @@ def private_relu(X, and_triples, r_arith, r_bin, mul_triple, seed, op_id, out=No
     return out
 
 
-def private_relu_fused(X, seed, op_id, out=None):
-    """ReLU with the dealer fused in: material from op ids op_id .. op_id + 3 (P = 2)."""
+def private_relu_fused(X, seed, op_id, out=None, add=None):
+    """ReLU with the dealer fused in: material from op ids op_id .. op_id + 3 (P = 2).
+    With `add` (shares shaped like X): the ReLU of X + add, the addition folded in."""
     P = X.shape[0]
     n = X.numel() // P
     out = torch.empty_like(X) if out is None else out
-    _check(_L().mpc_private_relu_fused(P, n, _ptr(X), _ptr(out), seed, op_id, _stream()))
+    if add is None:
+        _check(_L().mpc_private_relu_fused(P, n, _ptr(X), _ptr(out), seed, op_id, _stream()))
+    else:
+        if add.numel() != X.numel():
+            raise ValueError("add must have X's number of words")
+        _check(_L().mpc_private_relu_fused_add(P, n, _ptr(X), _ptr(add, "add"), _ptr(out), seed,
+                                               op_id, _stream()))
     return out
 
 

@@ -263,8 +263,11 @@ __global__ void __launch_bounds__(kThreads) ltz_kernel(i64 n, const u64* X, u64*
   }
 }
 
-__global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u64* X, u64* Y,
-                                                              u64 seed, u64 op) {
+// S (may be null): ReLU of X + S, the private addition of two sharings (local:
+// each party adds its shares) folded into the load.
+__global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u64* X,
+                                                              const u64* S, u64* Y, u64 seed,
+                                                              u64 op) {
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
   const int j = threadIdx.x & 3;
@@ -272,6 +275,10 @@ __global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u6
     const bool valid = i < n;
     const i64 blk = i >> 2;
     Sh2 x{{valid ? X[i] : 0ull, valid ? X[n + i] : 0ull}};
+    if (S && valid) {
+      x.v[0] += S[i];
+      x.v[1] += S[n + i];
+    }
     const Sh2 y = relu_quad(x, seed, op, blk, j);
     if (valid) {
       Y[i] = y.v[0];
@@ -629,6 +636,11 @@ int mpc_private_relu(int P, int64_t n, const uint64_t* X, uint64_t* Y,
 
 int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uint64_t seed,
                            uint64_t op_id, void* stream) {
+  return mpc_private_relu_fused_add(P, n, X, nullptr, Y, seed, op_id, stream);
+}
+
+int mpc_private_relu_fused_add(int P, int64_t n, const uint64_t* X, const uint64_t* S,
+                               uint64_t* Y, uint64_t seed, uint64_t op_id, void* stream) {
   if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
                           "fused private ReLU supports P = 2 (got %d)", P);
   MPC_REQUIRE(n >= 0, "negative length");
@@ -638,7 +650,7 @@ int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uin
   {
     KernelTimer timer("private_relu_fused", as_stream(stream));
     relu_fused_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, as_stream(stream)>>>(
-        n, (const u64*)X, (u64*)Y, seed, op_id);
+        n, (const u64*)X, (const u64*)S, (u64*)Y, seed, op_id);
     rc = check_launch("private_relu_fused");
   }
   if (rc == MPC_OK)

@@ -286,7 +286,12 @@ class PrivateResNet18:
                                   name + ".down")
                 else:
                     S = X
-                X = self.relu(api.add(Y, S), ops[name + ".relu2"])
+                if self.fused_relu:   # the residual sum folded into the ReLU's load
+                    P = Y.shape[0]
+                    X = api.private_relu_fused(Y.reshape(P, -1), self.seed, ops[name + ".relu2"],
+                                               add=S.reshape(P, -1)).view(Y.shape)
+                else:
+                    X = self.relu(api.add(Y, S), ops[name + ".relu2"])
             elif kind == "avgpool":
                 X = api.global_avgpool(X)
             elif kind == "fc":

@@ -361,6 +361,27 @@ def test_private_relu_fused_dealer(mpc, n, rng):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("n", [1, 1000, 50001])
+def test_private_relu_fused_add(mpc, n, rng):
+    """ReLU of a sum of two sharings (a residual connection) in one kernel: the
+    oracle's private addition then its private ReLU, word for word."""
+    v = rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)
+    u = rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)
+    X = sharing.share(v.view(np.uint64), 2, 0, SEED, 62)
+    S = sharing.share(u.view(np.uint64), 2, 1, SEED, 63)
+    op = 720
+    T = dealer.and_triples(2, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(2, n, SEED, op + 1)
+    mt = dealer.mul_triple(2, n, SEED, op + 2)
+    ref = binary.private_relu(X + S, T, ra, rb, mt, SEED, op + 3)
+    got = host(mpc.private_relu_fused(dev(X), SEED, op, add=dev(S)))
+    assert np.array_equal(got, ref)
+    # in place over X
+    dX = dev(X)
+    mpc.private_relu_fused(dX, SEED, op, out=dX, add=dev(S))
+    assert np.array_equal(host(dX), ref)
+
+
 # ---- square, affine, comparators, multiplexing ----------------------------------------
 @pytest.mark.parametrize("P", [1, 2, 3])
 def test_beaver_square(mpc, P, rng):
