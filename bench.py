@@ -579,6 +579,11 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "parties": 2, "batch": 1, "engine": args.algo,
+                   "dealer": "one step ahead on a low-priority stream, every step dealing one "
+                             "forward: the seven layers' convolution triples in one batched "
+                             "call (one limb GEMM launch), then each convolution's "
+                             "input-independent half prepared (F = W - B opened, weight-side "
+                             "and im2col(A_p) digit planes)",
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "ring_gemm_tops": 2 * macs * args.steps / (gemm_ms / 1e3) / 1e12 if gemm_ms else None,
