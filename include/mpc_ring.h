@@ -531,6 +531,18 @@ int mpc_private_relu_fused(int P, int64_t n, const uint64_t* X, uint64_t* Y, uin
 int mpc_private_relu_fused_add(int P, int64_t n, const uint64_t* X, const uint64_t* S,
                                uint64_t* Y, uint64_t seed, uint64_t op_id, void* stream);
 
+/* Private maximum of two sharings, P = 2 (§5.2 "Comparators"; the step of a
+ * max-pool tree): Y = B + ReLU(A - B), with the ReLU's dealer material that
+ * mpc_private_relu_fused (op ids op_id .. op_id + 3) draws for elements
+ * elem_offset .. elem_offset + n - 1 of a longer batch, so that the slices of
+ * one batched comparison (pair i of a tree level at elem_offset = i n) give
+ * the words of mpc_sub, one mpc_private_relu_fused over the whole batch and
+ * mpc_add.  elem_offset a non-negative multiple of 4 (MPC_EINVAL otherwise).
+ * A, B, Y device u64 [2][n]; Y may alias A or B.  The rounds of the batch are
+ * counted once, by the slice at offset 0. */
+int mpc_private_max_fused(int P, int64_t n, const uint64_t* A, const uint64_t* B, uint64_t* Y,
+                          uint64_t seed, uint64_t op_id, int64_t elem_offset, void* stream);
+
 /* ---- function approximations (App. D.2), two parties, fused dealer -------- */
 /* Each call below evaluates one function elementwise on two-party shares of
  * fixed-point values (2^16) in ONE launch per element range: every dealer

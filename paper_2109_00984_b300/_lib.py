@@ -95,6 +95,7 @@ SIGNATURES = {
     "mpc_affine": (c_int, [c_int, c_i64, c_vp, c_vp, c_i64, c_u64, c_int, c_vp]),
     "mpc_private_relu_fused": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_vp]),
     "mpc_private_relu_fused_add": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_u64, c_u64, c_vp]),
+    "mpc_private_max_fused": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_u64, c_u64, c_i64, c_vp]),
     "mpc_exp": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_vp]),
     "mpc_reciprocal": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_int, c_vp]),
     "mpc_sigmoid": (c_int, [c_int, c_i64, c_vp, c_vp, c_u64, c_u64, c_int, c_int, c_vp]),

@@ -541,6 +541,19 @@ def private_relu_fused(X, seed, op_id, out=None, add=None):
     return out
 
 
+def private_max_fused(A, B, seed, op_id, elem_offset=0, out=None):
+    """max(A, B) = B + ReLU(A - B) on two-party shares (P = 2), the ReLU's material
+    that of elements elem_offset .. of a batched comparison at op ids op_id .. + 3."""
+    P = A.shape[0]
+    n = A.numel() // P
+    if B.numel() != A.numel():
+        raise ValueError("A and B must have the same number of words")
+    out = torch.empty_like(A) if out is None else out
+    _check(_L().mpc_private_max_fused(P, n, _ptr(A), _ptr(B, "B"), _ptr(out), seed, op_id,
+                                      elem_offset, _stream()))
+    return out
+
+
 # ---- square, comparators, multiplexing ----------------------------------------------
 def ttp_square_pair(P, n, seed, op_id, device="cuda", out=None):
     A, B = out if out is not None else (_words((P, n), device), _words((P, n), device))

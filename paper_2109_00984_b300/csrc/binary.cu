@@ -264,22 +264,38 @@ __global__ void __launch_bounds__(kThreads) ltz_kernel(i64 n, const u64* X, u64*
 }
 
 // S (may be null): ReLU of X + S, the private addition of two sharings (local:
-// each party adds its shares) folded into the load.
+// each party adds its shares) folded into the load.  With max_mode, S + ReLU(X
+// - S) = max(X, S) instead (the comparison of a max-pool tree, both local
+// steps folded in).  blk_off: the dealer material of element i is that of
+// element i + 4 blk_off of a longer ReLU (a slice of a batched comparison).
 __global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u64* X,
                                                               const u64* S, u64* Y, u64 seed,
-                                                              u64 op) {
+                                                              u64 op, int max_mode,
+                                                              i64 blk_off) {
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
   const int j = threadIdx.x & 3;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < npad; i += stride) {
     const bool valid = i < n;
-    const i64 blk = i >> 2;
+    const i64 blk = (i >> 2) + blk_off;
     Sh2 x{{valid ? X[i] : 0ull, valid ? X[n + i] : 0ull}};
+    Sh2 s{{0ull, 0ull}};
     if (S && valid) {
-      x.v[0] += S[i];
-      x.v[1] += S[n + i];
+      s.v[0] = S[i];
+      s.v[1] = S[n + i];
     }
-    const Sh2 y = relu_quad(x, seed, op, blk, j);
+    if (max_mode) {
+      x.v[0] -= s.v[0];
+      x.v[1] -= s.v[1];
+    } else {
+      x.v[0] += s.v[0];
+      x.v[1] += s.v[1];
+    }
+    Sh2 y = relu_quad(x, seed, op, blk, j);
+    if (max_mode) {
+      y.v[0] += s.v[0];
+      y.v[1] += s.v[1];
+    }
     if (valid) {
       Y[i] = y.v[0];
       Y[n + i] = y.v[1];
@@ -650,11 +666,36 @@ int mpc_private_relu_fused_add(int P, int64_t n, const uint64_t* X, const uint64
   {
     KernelTimer timer("private_relu_fused", as_stream(stream));
     relu_fused_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, as_stream(stream)>>>(
-        n, (const u64*)X, (const u64*)S, (u64*)Y, seed, op_id);
+        n, (const u64*)X, (const u64*)S, (u64*)Y, seed, op_id, 0, 0);
     rc = check_launch("private_relu_fused");
   }
   if (rc == MPC_OK)
     stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,
+              (uint64_t)MPC_KS_GATES * n, (uint64_t)MPC_KS_GATES * 6ull * n + 2ull * n + 6ull * n,
+              0);
+  return rc;
+}
+
+int mpc_private_max_fused(int P, int64_t n, const uint64_t* A, const uint64_t* B, uint64_t* Y,
+                          uint64_t seed, uint64_t op_id, int64_t elem_offset, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "fused private max supports P = 2 (got %d)", P);
+  MPC_REQUIRE(n >= 0, "negative length");
+  MPC_REQUIRE(elem_offset >= 0 && elem_offset % 4 == 0,
+              "element offset %lld is not a non-negative multiple of 4", (long long)elem_offset);
+  if (n == 0) return MPC_OK;
+  MPC_REQUIRE(A && B && Y, "null pointer");
+  int rc;
+  {
+    KernelTimer timer("private_relu_fused", as_stream(stream));
+    relu_fused_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, as_stream(stream)>>>(
+        n, (const u64*)A, (const u64*)B, (u64*)Y, seed, op_id, 1, elem_offset / 4);
+    rc = check_launch("private_max_fused");
+  }
+  // the slices of one batched comparison share its rounds: counted once, by
+  // the slice at offset 0
+  if (rc == MPC_OK)
+    stats_add(elem_offset == 0 ? 9 : 0, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,
               (uint64_t)MPC_KS_GATES * n, (uint64_t)MPC_KS_GATES * 6ull * n + 2ull * n + 6ull * n,
               0);
   return rc;

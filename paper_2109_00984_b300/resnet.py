@@ -215,6 +215,17 @@ class PrivateResNet18:
         level = 0
         while len(vals) > 1:
             npairs = len(vals) // 2
+            if self.fused_relu and n % 4 == 0:
+                # pair i of the level: b + ReLU(a - b) in one kernel, the ReLU's
+                # material that of elements i n .. of the level's batched ReLU
+                new = [api.private_max_fused(vals[2 * i], vals[2 * i + 1], self.seed,
+                                             ops[level], elem_offset=i * n)
+                       for i in range(npairs)]
+                if len(vals) % 2:
+                    new.append(vals[-1])
+                vals = new
+                level += 1
+                continue
             D = torch.empty((P, npairs, n), dtype=torch.int64, device=self.device)
             for i in range(npairs):
                 api.sub(vals[2 * i], vals[2 * i + 1], out=D[:, i])

@@ -382,6 +382,28 @@ def test_private_relu_fused_add(mpc, n, rng):
     assert np.array_equal(host(dX), ref)
 
 
+def test_private_max_fused_slices(mpc, rng):
+    """max(A_i, B_i) = B_i + ReLU(A_i - B_i) pair by pair, each slice taking the
+    material of its elements in one batched ReLU over both pairs: the oracle's
+    subtraction, one private ReLU over the batch, and addition, word for word."""
+    n = 1000
+    A = [sharing.share(rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64).view(np.uint64),
+                       2, 0, SEED, 70 + i) for i in range(2)]
+    B = [sharing.share(rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64).view(np.uint64),
+                       2, 1, SEED, 80 + i) for i in range(2)]
+    op = 740
+    D = np.concatenate([A[i] - B[i] for i in range(2)], axis=1)
+    T = dealer.and_triples(2, 2 * n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(2, 2 * n, SEED, op + 1)
+    mt = dealer.mul_triple(2, 2 * n, SEED, op + 2)
+    R = binary.private_relu(D, T, ra, rb, mt, SEED, op + 3)
+    for i in range(2):
+        got = host(mpc.private_max_fused(dev(A[i]), dev(B[i]), SEED, op, elem_offset=i * n))
+        assert np.array_equal(got, B[i] + R[:, i * n:(i + 1) * n])
+    with pytest.raises(mpc.MPCError):
+        mpc.private_max_fused(dev(A[0]), dev(B[0]), SEED, op, elem_offset=3)
+
+
 # ---- square, affine, comparators, multiplexing ----------------------------------------
 @pytest.mark.parametrize("P", [1, 2, 3])
 def test_beaver_square(mpc, P, rng):

@@ -51,9 +51,13 @@ def test_global_avgpool(mpc, rng):
     assert np.array_equal(got, oresnet.global_avgpool_shares(X))
 
 
-def test_maxpool_tree(mpc, rng):
+@pytest.mark.parametrize("shape", [
+    (2, 4, 11, 10),   # 120 outputs: the fused comparison per pair (a multiple of 4)
+    (2, 3, 9, 9),     # 75 outputs: the batched sub / ReLU / add fallback
+])
+def test_maxpool_tree(mpc, rng, shape):
     from paper_2109_00984_b300.resnet import PrivateResNet18
-    v = rng.integers(0, 1 << 40, (2, 4, 11, 10)).astype(np.int64)
+    v = rng.integers(0, 1 << 40, shape).astype(np.int64)
     X = sharing.share(v.view(np.uint64), 2, 0, 1, 3)
     net = PrivateResNet18({}, [], synth.resnet_schedule(), fused_relu=False)
     got = host(net.maxpool(dev(X), 3, 2, 1, [101, 111, 121, 131]))
