@@ -26,21 +26,32 @@ __global__ void __launch_bounds__(kThreads) addsub_kernel(int P, i64 n, const u6
 }
 
 // taps[t][p][b][c][oh][ow] = X[p][b][c][oh*sh + r - ph][ow*sw + s - pw] (0 outside),
-// t = r * kw + s.
+// t = r * kw + s.  One thread per output position (b, c, oh, ow) writes all its
+// taps for every party: the position is decoded once (three 64-bit divisions)
+// instead of once per tap and party; the writes of consecutive threads stay
+// consecutive within each (t, p) plane.
 __global__ void __launch_bounds__(kThreads) taps_kernel(int P, mpc_conv_desc d, i64 ho, i64 wo,
                                                         const u64* __restrict__ X,
                                                         u64* __restrict__ taps) {
   const i64 nout = d.batch * d.c_in * ho * wo;
   const i64 nin = d.batch * d.c_in * d.h * d.w;
-  const i64 total = d.kh * d.kw * P * nout;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < total;
-       i += (i64)gridDim.x * blockDim.x) {
-    const i64 e = i % nout, tp = i / nout;
-    const i64 p = tp % P, t = tp / P;
-    const i64 r = t / d.kw, s = t % d.kw;
-    const i64 ow = e % wo, oh = (e / wo) % ho, bc = e / (wo * ho);
-    const i64 y = oh * d.stride_h + r - d.pad_h, x = ow * d.stride_w + s - d.pad_w;
-    taps[i] = (y >= 0 && y < d.h && x >= 0 && x < d.w) ? X[p * nin + (bc * d.h + y) * d.w + x] : 0ull;
+  const int kh = (int)d.kh, kw = (int)d.kw;
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < nout;
+       e += (i64)gridDim.x * blockDim.x) {
+    const i64 ow = e % wo, q = e / wo;
+    const i64 oh = q % ho, bc = q / ho;
+    const i64 y0 = oh * d.stride_h - d.pad_h, x0 = ow * d.stride_w - d.pad_w;
+    for (int r = 0; r < kh; ++r) {
+      const i64 y = y0 + r;
+      const bool yin = y >= 0 && y < d.h;
+      for (int s = 0; s < kw; ++s) {
+        const i64 x = x0 + s;
+        const bool in = yin && x >= 0 && x < d.w;
+        const i64 src = (bc * d.h + y) * d.w + x;
+        u64* dst = taps + (i64)(r * kw + s) * P * nout + e;
+        for (int p = 0; p < P; ++p) dst[(i64)p * nout] = in ? X[p * nin + src] : 0ull;
+      }
+    }
   }
 }
 
@@ -106,8 +117,8 @@ int mpc_window_taps(int P, const mpc_conv_desc* d, const uint64_t* X, uint64_t* 
   MPC_REQUIRE(X && taps, "null pointer");
   const i64 ho = (d->h + 2 * d->pad_h - d->kh) / d->stride_h + 1;
   const i64 wo = (d->w + 2 * d->pad_w - d->kw) / d->stride_w + 1;
-  const i64 total = d->kh * d->kw * P * d->batch * d->c_in * ho * wo;
-  taps_kernel<<<grid_for(total, kThreads), kThreads, 0, as_stream(stream)>>>(P, *d, ho, wo,
+  const i64 nout = d->batch * d->c_in * ho * wo;
+  taps_kernel<<<grid_for(nout, kThreads), kThreads, 0, as_stream(stream)>>>(P, *d, ho, wo,
                                                                            (const u64*)X,
                                                                            (u64*)taps);
   return check_launch("window_taps");
