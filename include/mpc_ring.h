@@ -318,6 +318,33 @@ int mpc_beaver_conv2d_relu_prepared(int P, const mpc_conv_desc* d, const uint64_
                                     size_t prep_bytes, uint64_t* Y, int trunc_bits, uint64_t seed,
                                     uint64_t relu_op, void* ws, size_t ws_bytes, void* stream);
 
+/* Prepared products (limb engine): the preparation goes one step further and
+ * also computes each party's input-independent product, C'_p = C_p + A_p F
+ * with F = W - B opened (App. D.1.1: Z_p = C_p + E B_p + A_p F + [p = 0] E F),
+ * so the online half is one operand pair per party, Z_p = C'_p + E G_p with
+ * G_0 = B_0 + F and G_p = B_p.  prep (device, mpc_conv2d_prep_products_size
+ * bytes) receives the digit planes of G_0 .. G_{P-1} and C'_0 .. C'_{P-1};
+ * the preparation uses ws (mpc_conv2d_prepare_products_workspace_size bytes).
+ * The online calls read neither W, B nor C, and give the words of
+ * mpc_beaver_conv2d / mpc_beaver_conv2d_relu with the same triple (ws as
+ * mpc_conv2d_workspace_size(P, d, MPC_ALGO_LIMB)).  The sizes are 0 for
+ * invalid arguments or shapes outside the limb engine. */
+size_t mpc_conv2d_prep_products_size(int P, const mpc_conv_desc* d);
+size_t mpc_conv2d_prepare_products_workspace_size(int P, const mpc_conv_desc* d);
+int mpc_beaver_conv2d_prepare_products(int P, const mpc_conv_desc* d, const uint64_t* W,
+                                       const uint64_t* A, const uint64_t* B, const uint64_t* C,
+                                       void* prep, size_t prep_bytes, void* ws, size_t ws_bytes,
+                                       void* stream);
+int mpc_beaver_conv2d_prepared_products(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                        const uint64_t* A, const void* prep, size_t prep_bytes,
+                                        uint64_t* Z, int trunc_bits, void* ws, size_t ws_bytes,
+                                        void* stream);
+int mpc_beaver_conv2d_relu_prepared_products(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                             const uint64_t* A, const void* prep,
+                                             size_t prep_bytes, uint64_t* Y, int trunc_bits,
+                                             uint64_t seed, uint64_t relu_op, void* ws,
+                                             size_t ws_bytes, void* stream);
+
 /* Beaver matmul that allocates nothing (the paper has no counterpart: this is
  * an interface for callers that can neither allocate device memory when they
  * call the library nor hand it a workspace, e.g. a host program whose device

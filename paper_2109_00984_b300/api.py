@@ -297,6 +297,59 @@ def beaver_conv2d_prepared(X, A, C, prep, d, trunc_bits=0, out=None, ws=None):
     return Z
 
 
+def conv2d_prep_products_size(P, d):
+    return int(_L().mpc_conv2d_prep_products_size(P, ctypes.byref(d)))
+
+
+def conv2d_prepare_products_workspace_size(P, d):
+    return int(_L().mpc_conv2d_prepare_products_workspace_size(P, ctypes.byref(d)))
+
+
+def beaver_conv2d_prepare_products(W, A, B, C, d, out=None, ws=None):
+    """Input-independent half of a limb-engine Beaver convolution including each
+    party's product: C'_p = C_p + A_p F (F = W - B opened) and the planes of
+    G_p (G_0 = B_0 + F, G_p = B_p); returns the uint8 device buffer holding them."""
+    P = W.shape[0]
+    need = conv2d_prep_products_size(P, d)
+    if need == 0:
+        raise MPCError(-6, "no prepared products for this convolution shape")
+    prep = torch.empty(need, dtype=torch.uint8, device=W.device) if out is None else out
+    wneed = conv2d_prepare_products_workspace_size(P, d)
+    ws = _ws(wneed, W.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_prepare_products(
+        P, ctypes.byref(d), _ptr(W), _ptr(A), _ptr(B), _ptr(C), _ptr(prep, "prep", torch.uint8),
+        prep.numel(), _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return prep
+
+
+def beaver_conv2d_prepared_products(X, A, prep, d, trunc_bits=0, out=None, ws=None):
+    """Online half on prepared products (one operand pair per party); equals
+    beaver_conv2d(..., algo=LIMB) with the same triple."""
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Z = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), LIMB)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_prepared_products(
+        P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(prep, "prep", torch.uint8), prep.numel(),
+        _ptr(Z), trunc_bits, _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return Z
+
+
+def beaver_conv2d_relu_prepared_products(X, A, prep, d, seed, relu_op, trunc_bits=0, out=None,
+                                         ws=None):
+    """beaver_conv2d_prepared_products then the fused private ReLU (two parties)."""
+    P = X.shape[0]
+    ho, wo = conv_out_hw(d)
+    Y = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
+    need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), LIMB)
+    ws = _ws(need, X.device) if ws is None else ws
+    _check(_L().mpc_beaver_conv2d_relu_prepared_products(
+        P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(prep, "prep", torch.uint8), prep.numel(),
+        _ptr(Y), trunc_bits, seed, relu_op, _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    return Y
+
+
 def beaver_conv2d_relu_prepared(X, A, C, prep, d, seed, relu_op, trunc_bits=0, out=None,
                                 ws=None):
     """beaver_conv2d_prepared then the fused private ReLU (two parties); equals

@@ -62,6 +62,11 @@ struct GemmArgs {
   // every job's B2 are taken from there; only the opened gather B1 is cut in
   // the call.  jobs[j].A1 / A2 / B2 are then unused.
   const void* prep;
+  // With prep: 2 (default 0 means 2) for the layout above; 1 for prepared
+  // products: prep holds only job j's A1 planes (plane set j), the products
+  // A_p F having been added into C by the preparation, so each job is one pair
+  // (its A1 planes times the opened gather B1).
+  int prep_pairs;
   GemmJob jobs[MPC_MAX_PARTIES];
 };
 
@@ -74,7 +79,9 @@ int choose_splits(i64 tiles, i64 units, i64 min_units);
 
 // Per-engine split choice (deterministic in the shape) and partial-sum bytes.
 int plain_splits(i64 M, i64 N, i64 K, int npairs, int njobs);
-int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs);
+// batch: a batch of one-pair products dealt beside the online phase (per-job
+// gathers), split into fewer, longer pieces.
+int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs, bool batch = false);
 inline size_t partial_bytes(int splits, int njobs, i64 M, i64 N) {
   return splits > 1 ? (size_t)splits * njobs * M * N * sizeof(u64) : 0;
 }
@@ -127,6 +134,11 @@ int limb_conv_prepare(int P, const ConvGather& cg, i64 M, i64 N, i64 K,
                       const u64* const* asrc, void* prep, cudaStream_t s);
 bool limb_supported(i64 M, i64 N, i64 K);
 
+// The digit planes of n row-major [M][K] sources src[i] into out, one plane set
+// of al256(16 M K1p) bytes per source (K1p = K rounded up to 16), in order.
+int limb_cut_planes_a(int n, const u64* const* src, i64 M, i64 K, void* out, cudaStream_t s);
+size_t limb_planes_a_bytes(i64 M, i64 K);
+
 // Grouped limb engine: the Beaver products of a batch in one digit-plane launch
 // (which also opens E and F) and one persistent GEMM launch.  Per product and
 // party p:
@@ -147,8 +159,8 @@ int launch_gemm_limb_grouped(int P, int count, const GroupedProduct* prods, int 
 
 // Engine dispatch shared by the entry points: split choice, workspace bytes
 // (split-K partials, then limb planes) and the launch of one GEMM job set.
-int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
-size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs);
+int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs, bool batch = false);
+size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs, bool batch = false);
 // used (optional): the job set as launched (split count, partial buffer).
 int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s,
              GemmArgs* used = nullptr);

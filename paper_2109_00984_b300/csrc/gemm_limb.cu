@@ -1440,7 +1440,7 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs) {
+int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs, bool batch) {
   const i64 tiles = ceil_div(M, BM) * ceil_div(N, BN) * njobs;
   // A batch of one-pair products (the dealer's triples of same-shaped layers,
   // dealt on a low-priority stream beside the online phase) takes splits of
@@ -1448,7 +1448,7 @@ int limb_splits(i64 M, i64 N, i64 K, int npairs, int njobs) {
   // splits (252 CTAs of 38 sub-steps) instead of 7 (588 CTAs of 16), which
   // spends less of each CTA on its fixed set-up, fill and epilogue: the
   // dealer alone 6 % faster and the overlapped step 1 % faster.
-  const i64 min_units = (npairs == 1 && njobs > 1) ? 32 : 16;
+  const i64 min_units = batch ? 32 : 16;
   return choose_splits(tiles, npairs * pair_k(K) / KS, min_units);
 }
 
@@ -1508,6 +1508,32 @@ int limb_conv_prepare(int P, const ConvGather& cg, i64 M, i64 N, i64 K,
   return check_launch("limb_planes");
 }
 
+size_t limb_planes_a_bytes(i64 M, i64 K) { return al256((size_t)16 * M * pair_k(K)); }
+
+int limb_cut_planes_a(int n, const u64* const* src, i64 M, i64 K, void* out, cudaStream_t s) {
+  if (n <= 0 || M <= 0 || K <= 0) return MPC_OK;
+  if (n > 2 * MPC_MAX_PARTIES) return fail(MPC_EINVAL, "too many plane sources");
+  const i64 K1p = pair_k(K);
+  const size_t bytes = limb_planes_a_bytes(M, K);
+  KernelTimer timer("limb_planes", s);
+  PlanesLaunch pl;
+  memset(&pl, 0, sizeof(pl));
+  for (int i = 0; i < n; ++i)
+    pl.ja.j[i] = PlaneJob{src[i], nullptr,
+                          reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(out) + i * bytes)};
+  pl.M = M;
+  pl.N = 1;
+  pl.K = K;
+  pl.Kp = K1p;
+  pl.na = n;
+  pl.nb = 0;
+  pl.bx = pl.by = 1;
+  pl.a_blk = (int)std::min<i64>(ceil_div(M * (K1p / 8), 256), 148 * 4);
+  const i64 blocks = (i64)n * pl.a_blk;
+  limb_planes<false><<<(unsigned)blocks, 256, 0, s>>>(pl);
+  return check_launch("limb_planes");
+}
+
 int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream_t s) {
   GemmArgs g = g_in;
   if (g.splits < 1) g.splits = 1;
@@ -1519,7 +1545,8 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   const bool prep = g.prep != nullptr;
   if (prep && g.gather == nullptr)
     return fail(MPC_EINVAL, "limb engine: prepared planes need the convolution gather");
-  const int npairs = (prep || g.jobs[0].A2) ? 2 : 1;
+  const bool prep1 = prep && g.prep_pairs == 1;  // prepared products: one pair per job
+  const int npairs = ((prep && !prep1) || (!prep && g.jobs[0].A2)) ? 2 : 1;
   const bool per_job = g.gather != nullptr && g.gather_per_job != 0;
   if (per_job && (npairs != 1 || prep))
     return fail(MPC_EINVAL, "limb engine: per-job gathers take one-pair products");
@@ -1549,6 +1576,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
   if (prep) {
     for (int j = 0; j < g.njobs; ++j) {
       if (int rc = encode_planes(&prm.tmA[0][j], pp + (size_t)j * a_bytes, g.M, K1p, BM)) return rc;
+      if (prep1) continue;
       if (int rc = encode_planes(&prm.tmA[1][j], pp + (size_t)g.njobs * a_bytes, g.M, K1p, BM))
         return rc;
     }
@@ -1620,7 +1648,7 @@ int launch_gemm_limb(const GemmArgs& g_in, void* ws, size_t ws_bytes, cudaStream
     }
     for (int j = 0; j < g.njobs; ++j) {
       if (int rc = encode_planes(&prm.tmB[0][j], jbv.j[0].out, g.N, K1p, BN)) return rc;
-      if (prep) {
+      if (prep && !prep1) {
         const char* bj = pp + (size_t)(g.njobs + 1) * a_bytes + (size_t)j * b_bytes;
         if (int rc = encode_planes(&prm.tmB[1][j], bj, g.N, K1p, BN)) return rc;
       } else if (npairs == 2) {

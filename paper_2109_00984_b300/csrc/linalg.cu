@@ -361,14 +361,14 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
-  return algo == MPC_ALGO_LIMB ? limb_splits(M, N, K, npairs, njobs)
+int engine_splits(int algo, i64 M, i64 N, i64 K, int npairs, int njobs, bool batch) {
+  return algo == MPC_ALGO_LIMB ? limb_splits(M, N, K, npairs, njobs, batch)
                                : plain_splits(M, N, K, npairs, njobs);
 }
 
 // Engine workspace: split-K partial sums, then (limb) the digit planes.
-size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
-  const int sp = engine_splits(algo, M, N, K, npairs, njobs);
+size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs, bool batch) {
+  const int sp = engine_splits(algo, M, N, K, npairs, njobs, batch);
   size_t b = align256(partial_bytes(sp, njobs, M, N));
   if (algo == MPC_ALGO_LIMB) b += limb_workspace_bytes(M, N, K, npairs, njobs);
   return b;
@@ -377,7 +377,7 @@ size_t engine_ws(int algo, i64 M, i64 N, i64 K, int npairs, int njobs) {
 int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s, GemmArgs* used) {
   if (g.M <= 0 || g.N <= 0 || g.njobs <= 0) return MPC_OK;
   const int npairs = g.jobs[0].A2 ? 2 : 1;
-  g.splits = engine_splits(algo, g.M, g.N, g.K, npairs, g.njobs);
+  g.splits = engine_splits(algo, g.M, g.N, g.K, npairs, g.njobs, g.gather_per_job != 0);
   if (g.max_splits > 0 && g.splits > g.max_splits) g.splits = g.max_splits;
   const size_t pb = align256(partial_bytes(g.splits, g.njobs, g.M, g.N));
   if (ws_bytes < pb) return fail(MPC_ENOMEM, "engine workspace too small for split-K partials");
@@ -697,6 +697,164 @@ int mpc_beaver_conv2d_relu_prepared(int P, const mpc_conv_desc* d, const uint64_
   return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
 }
 
+// ---- prepared products: the dealer adds A_p F into C_p --------------------------
+namespace {
+
+struct ProdPrep {
+  i64 M, N, K, ho, wo, nx;
+  size_t planes, cwords;  // bytes of one plane set, of one party's C'
+};
+
+int prod_prep_shape(int P, const mpc_conv_desc* d, ProdPrep* q) {
+  MPC_CHECK_PARTIES(P);
+  i64 ho, wo;
+  if (int rc = validate_conv(d, &ho, &wo)) return rc;
+  q->M = d->c_out;
+  q->K = d->c_in * d->kh * d->kw;
+  q->N = d->batch * ho * wo;
+  q->ho = ho;
+  q->wo = wo;
+  q->nx = d->batch * d->c_in * d->h * d->w;
+  if (!limb_supported(q->M, q->N, q->K))
+    return fail(MPC_EUNSUPPORTED, "limb engine does not support this conv shape");
+  q->planes = limb_planes_a_bytes(q->M, q->K);
+  q->cwords = align256(words(q->M * q->N));
+  return MPC_OK;
+}
+
+// Online half of a convolution on prepared products: E opened and gathered,
+// one operand pair per party, C'_p from prep.
+int conv_prepared_products_impl(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                const uint64_t* A, const void* prep, size_t prep_bytes,
+                                uint64_t* Z, int trunc_bits, void* ws, size_t ws_bytes,
+                                cudaStream_t s, GemmArgs* deferred) {
+  ProdPrep q;
+  if (int rc = prod_prep_shape(P, d, &q)) return rc;
+  MPC_REQUIRE(trunc_bits >= 0 && trunc_bits <= 63, "trunc_bits %d outside [0, 63]", trunc_bits);
+  MPC_REQUIRE(X && A && prep && Z, "null pointer");
+  if (prep_bytes < mpc_conv2d_prep_products_size(P, d))
+    return fail(MPC_ENOMEM, "prep buffer %zu bytes, too small", prep_bytes);
+  const size_t need = engine_ws(MPC_ALGO_LIMB, q.M, q.N, q.K, 1, P);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  const char* cp = static_cast<const char*>(prep) + (size_t)P * q.planes;
+  ConvGather cg{};
+  cg.d = *d;
+  cg.ho = q.ho;
+  cg.wo = q.wo;
+  cg.src1 = (const u64*)X;
+  cg.sub1 = (const u64*)A;
+  cg.stride1 = q.nx;
+  cg.n1 = P;
+  GemmArgs g{};
+  g.prep = prep;
+  g.prep_pairs = 1;
+  g.M = q.M;
+  g.N = q.N;
+  g.K = q.K;
+  g.hw_out = q.ho * q.wo;
+  g.trunc_bits = trunc_bits;
+  g.njobs = P;
+  g.gather = &cg;
+  g.defer_reduce = deferred != nullptr;
+  for (int p = 0; p < P; ++p) {
+    g.jobs[p].C = reinterpret_cast<const u64*>(cp + (size_t)p * q.cwords);
+    g.jobs[p].Z = (u64*)Z + (i64)p * q.M * q.N;
+  }
+  const int rc = run_gemm(g, MPC_ALGO_LIMB, ws, ws_bytes, s, deferred);
+  if (rc == MPC_OK)
+    stats_add(1, 8ull * (uint64_t)q.nx, 0, (uint64_t)P * (uint64_t)q.nx,
+              (uint64_t)P * (uint64_t)(q.M * q.N * q.K));
+  return rc;
+}
+
+}  // namespace
+
+size_t mpc_conv2d_prep_products_size(int P, const mpc_conv_desc* d) {
+  ProdPrep q;
+  if (P < 1 || P > MPC_MAX_PARTIES || prod_prep_shape(P, d, &q) != MPC_OK) return 0;
+  return (size_t)P * (q.planes + q.cwords);
+}
+
+size_t mpc_conv2d_prepare_products_workspace_size(int P, const mpc_conv_desc* d) {
+  ProdPrep q;
+  if (P < 1 || P > MPC_MAX_PARTIES || prod_prep_shape(P, d, &q) != MPC_OK) return 0;
+  return 2 * align256(words(q.M * q.K)) + engine_ws(MPC_ALGO_LIMB, q.M, q.N, q.K, 1, P, true);
+}
+
+int mpc_beaver_conv2d_prepare_products(int P, const mpc_conv_desc* d, const uint64_t* W,
+                                       const uint64_t* A, const uint64_t* B, const uint64_t* C,
+                                       void* prep, size_t prep_bytes, void* ws, size_t ws_bytes,
+                                       void* stream) {
+  ProdPrep q;
+  if (int rc = prod_prep_shape(P, d, &q)) return rc;
+  MPC_REQUIRE(W && A && B && C && prep, "null pointer");
+  if (prep_bytes < (size_t)P * (q.planes + q.cwords))
+    return fail(MPC_ENOMEM, "prep buffer %zu bytes, need %zu", prep_bytes,
+                (size_t)P * (q.planes + q.cwords));
+  const size_t need = mpc_conv2d_prepare_products_workspace_size(P, d);
+  MPC_REQUIRE(ws != nullptr, "null workspace");
+  if (ws_bytes < need) return fail(MPC_ENOMEM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  Carve cv(ws);
+  u64* F = cv.take(q.M * q.K);
+  u64* G = cv.take(q.M * q.K);
+  // F = sum_p (W_p - B_p) opened, G = B_0 + F
+  MPC_DISPATCH_P(P, launch_open, q.M * q.K, (const u64*)W, (const u64*)B, F, (const u64*)B, G, s);
+  if (int rc = check_launch("open F")) return rc;
+  // C'_p = C_p + A_p F: one one-pair job per party, F times its own im2col(A_p)
+  char* cp = static_cast<char*>(prep) + (size_t)P * q.planes;
+  ConvGather cg[MPC_MAX_PARTIES] = {};
+  GemmArgs g{};
+  g.M = q.M;
+  g.N = q.N;
+  g.K = q.K;
+  g.hw_out = q.ho * q.wo;
+  g.njobs = P;
+  g.gather = cg;
+  g.gather_per_job = 1;
+  for (int p = 0; p < P; ++p) {
+    cg[p].d = *d;
+    cg[p].ho = q.ho;
+    cg[p].wo = q.wo;
+    cg[p].src2[0] = (const u64*)A + (i64)p * q.nx;
+    g.jobs[p] = GemmJob{F, nullptr, nullptr, nullptr, (const u64*)C + (i64)p * q.M * q.N,
+                        reinterpret_cast<u64*>(cp + (size_t)p * q.cwords)};
+  }
+  if (int rc = run_gemm(g, MPC_ALGO_LIMB, cv.rest(), ws_bytes - cv.off, s, nullptr)) return rc;
+  // digit planes of the first-pair weights G, B_1 .. B_{P-1}
+  const u64* asrc[MPC_MAX_PARTIES];
+  asrc[0] = G;
+  for (int p = 1; p < P; ++p) asrc[p] = (const u64*)B + (i64)p * q.M * q.K;
+  if (int rc = limb_cut_planes_a(P, asrc, q.M, q.K, prep, s)) return rc;
+  stats_add(1, 8ull * (uint64_t)(q.M * q.K), 0, 0, (uint64_t)P * (uint64_t)(q.M * q.N * q.K));
+  return MPC_OK;
+}
+
+int mpc_beaver_conv2d_prepared_products(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                        const uint64_t* A, const void* prep, size_t prep_bytes,
+                                        uint64_t* Z, int trunc_bits, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  return conv_prepared_products_impl(P, d, X, A, prep, prep_bytes, Z, trunc_bits, ws, ws_bytes,
+                                     as_stream(stream), nullptr);
+}
+
+int mpc_beaver_conv2d_relu_prepared_products(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                             const uint64_t* A, const void* prep,
+                                             size_t prep_bytes, uint64_t* Y, int trunc_bits,
+                                             uint64_t seed, uint64_t relu_op, void* ws,
+                                             size_t ws_bytes, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "convolution + fused ReLU supports P = 2 (got %d)", P);
+  GemmArgs used{};
+  used.njobs = 0;
+  if (int rc = conv_prepared_products_impl(P, d, X, A, prep, prep_bytes, Y, trunc_bits, ws,
+                                           ws_bytes, as_stream(stream), &used))
+    return rc;
+  if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
+  return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
+}
+
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo) {
   if (!gemm_shape_fits(M, N, K)) return 0;
   return engine_ws(resolve_algo(algo, M, N, K), M, N, K, 1, 1);
@@ -865,7 +1023,7 @@ size_t mpc_conv2d_triples_workspace_size(int P, int count, const mpc_conv_desc* 
     for (int j = 0; j < count; ++j) need = std::max(need, conv_triple_ws(d[j], tb.ho, tb.wo, algo));
     return need;
   }
-  size_t need = engine_ws(MPC_ALGO_LIMB, tb.M, tb.N, tb.Kmax, 1, count);
+  size_t need = engine_ws(MPC_ALGO_LIMB, tb.M, tb.N, tb.Kmax, 1, count, true);
   for (int j = 0; j < count; ++j)
     need += align256(words(d[j].batch * d[j].c_in * d[j].h * d[j].w)) +
             align256(words(tb.M * d[j].c_in * d[j].kh * d[j].kw));

@@ -36,7 +36,7 @@ def _same_output(a, b):
 class PrivateConv1dStack:
     def __init__(self, weights, strides, pads, frames, batch=1, algo=api.PLAIN, frac_bits=16,
                  weight_ops=None, seed=1, device="cuda", fused_relu=True, overlap_dealer=True,
-                 prepare_weights=False, batch_triples=True):
+                 prepare_weights=False, batch_triples=True, prepare_products=False):
         self.P = 2
         self.fused_relu = fused_relu
         # deal the triples of consecutive layers with one output shape in one
@@ -61,7 +61,7 @@ class PrivateConv1dStack:
         self.out_len = L
         self.in_shape = (batch, weights[0].shape[1], frames)
         self._alloc()
-        self.enable_prepared(prepare_weights)
+        self.enable_prepared(prepare_weights or prepare_products, products=prepare_products)
 
     def _alloc(self):
         P, dev = self.P, self.device
@@ -108,6 +108,7 @@ class PrivateConv1dStack:
             ws_bytes = max(ws_bytes, api.conv2d_triples_workspace_size(
                 P, count, self.descs[first:first + count], self.algo))
         self.prepared = False
+        self.prep_products = False
         self.prep = None
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         self.dealer_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -120,7 +121,7 @@ class PrivateConv1dStack:
         self.out_real = torch.empty((self.in_shape[0], self.descs[-1].c_out, self.out_len),
                                     dtype=torch.float64, device=dev)
 
-    def enable_prepared(self, on=True):
+    def enable_prepared(self, on=True, products=False):
         """With `on` (limb engine, fused ReLU) the input-independent half of each
         convolution -- opening F = W - B, the weight-side digit planes and those
         of im2col(A_p) -- is done by the dealer right after the layer's triple,
@@ -128,12 +129,23 @@ class PrivateConv1dStack:
         phase only cuts im2col(E) before its GEMM.  That shortens the online
         phase (its latency) and, with the dealer's triples batched, also raises
         the overlapped throughput (the dealer's launches fit the online phase's
-        gaps).  Takes effect from the next deal."""
+        gaps).  With `products` the dealer also computes each party's product
+        A_p F into C (mpc_beaver_conv2d_prepare_products), so the online GEMM
+        is one operand pair per party.  Takes effect from the next deal."""
+        size = api.conv2d_prep_products_size if products else api.conv2d_prep_size
         ok = on and self.fused_relu and self.algo != api.PLAIN and all(
-            api.conv2d_prep_size(self.P, d) > 0 for d in self.descs)
-        if ok and self.prep is None:
-            self.prep = [[torch.empty(api.conv2d_prep_size(self.P, d), dtype=torch.uint8,
-                                      device=self.device) for d in self.descs] for _ in range(2)]
+            size(self.P, d) > 0 for d in self.descs)
+        if ok and (self.prep is None or self.prep_products != products):
+            self.prep = [[torch.empty(size(self.P, d), dtype=torch.uint8, device=self.device)
+                          for d in self.descs] for _ in range(2)]
+            if products:
+                need = max(api.conv2d_prepare_products_workspace_size(self.P, d)
+                           for d in self.descs)
+                if self.dealer_ws.numel() < need:
+                    self.dealer_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+                if self.ws.numel() < need:
+                    self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        self.prep_products = ok and products
         self.prepared = ok
 
     def deal(self, schedule, slot=0, join=False):
@@ -162,7 +174,11 @@ class PrivateConv1dStack:
                                            self.algo, outs=outs, ws=ws)
                 for l in layers:
                     t = self.trip[slot][l]
-                    if self.prepared:
+                    if self.prep_products:
+                        api.beaver_conv2d_prepare_products(self.W[l], t["A"], t["B"], t["C"],
+                                                           self.descs[l], out=self.prep[slot][l],
+                                                           ws=ws)
+                    elif self.prepared:
                         api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], self.descs[l],
                                                   out=self.prep[slot][l])
                     if ds is not main:
@@ -223,7 +239,10 @@ class PrivateConv1dStack:
             if deal:
                 api.ttp_conv2d_triple(self.P, d, seed, ops["conv"], self.algo,
                                       out=(t["A"], t["B"], t["C"]), ws=self.ws)
-                if self.prepared:
+                if self.prep_products:
+                    api.beaver_conv2d_prepare_products(self.W[l], t["A"], t["B"], t["C"], d,
+                                                       out=self.prep[slot][l], ws=self.ws)
+                elif self.prepared:
                     api.beaver_conv2d_prepare(self.W[l], t["A"], t["B"], d,
                                               out=self.prep[slot][l])
             elif wait_dealer and self.ready[slot][l] is not None:
@@ -234,7 +253,11 @@ class PrivateConv1dStack:
                                                                  ops["and"] + 3)
                 # convolution + truncation + ReLU: the ReLU kernel reduces the
                 # GEMM's split-K partial sums itself
-                if self.prepared:
+                if self.prep_products:
+                    api.beaver_conv2d_relu_prepared_products(
+                        X, t["A"], self.prep[slot][l], d, seed, ops["and"],
+                        trunc_bits=self.frac_bits, out=b["Y"], ws=self.ws)
+                elif self.prepared:
                     api.beaver_conv2d_relu_prepared(X, t["A"], t["C"], self.prep[slot][l], d,
                                                     seed, ops["and"], trunc_bits=self.frac_bits,
                                                     out=b["Y"], ws=self.ws)

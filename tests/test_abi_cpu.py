@@ -200,3 +200,27 @@ def test_conv_triples_batch_validation(lib):
     assert call(3, descs=(_lib.ConvDesc * 3)(d, other, d)) == E["EINVAL"]
     assert call(3, descs=None) == E["EINVAL"]
     assert call(3, ws_bytes=three - 1) == E["ENOMEM"]
+
+
+def test_prepared_products_validation(lib):
+    from paper_2109_00984_b300 import _lib
+    d = _lib.ConvDesc(1, 16, 1, 64, 32, 1, 7, 1, 1, 0, 3)
+    dp = ctypes.byref(d)
+    need = lib.mpc_conv2d_prep_products_size(2, dp)
+    K1p = 16 * 7
+    assert need >= 2 * (16 * 32 * K1p + 8 * 32 * 64)
+    assert lib.mpc_conv2d_prep_products_size(0, dp) == 0
+    wneed = lib.mpc_conv2d_prepare_products_workspace_size(2, dp)
+    assert wneed > 0
+    assert lib.mpc_beaver_conv2d_prepare_products(2, dp, FAKE, FAKE, FAKE, FAKE, FAKE, need - 1,
+                                                  FAKE, wneed, NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_conv2d_prepare_products(2, dp, FAKE, FAKE, FAKE, FAKE, FAKE, need,
+                                                  FAKE, wneed - 1, NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_conv2d_prepare_products(2, dp, FAKE, FAKE, NULL, FAKE, FAKE, need,
+                                                  FAKE, wneed, NULL) == E["EINVAL"]
+    assert lib.mpc_beaver_conv2d_prepared_products(2, dp, FAKE, FAKE, FAKE, need - 1, FAKE, 16,
+                                                   FAKE, 1 << 30, NULL) == E["ENOMEM"]
+    assert lib.mpc_beaver_conv2d_relu_prepared_products(3, dp, FAKE, FAKE, FAKE, need, FAKE, 16,
+                                                        1, 1, FAKE, 1 << 30, NULL) == \
+        E["EUNSUPPORTED"]
+

@@ -118,3 +118,49 @@ def test_prepared_conv2d_more_parties(mpc, P, rng):
     Zp = mpc.beaver_conv2d_prepared(dev(X), dA, dev(C), prep, d, trunc_bits=16)
     mpc.sync_status()
     assert np.array_equal(host(Zp), Z)
+
+
+@pytest.mark.parametrize("geom", GEOMS)
+def test_prepared_products_conv2d_relu_matches_oracle(mpc, geom, rng):
+    """The preparation also adds each party's input-independent product A_p F
+    into C; the online half is one operand pair per party (E G_p): the oracle's
+    words, with the ReLU and without it."""
+    b, ci, h, w, co, kh, kw, st, ph, pw = geom
+    P = 2
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 93, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    n = Z[0].size
+    op = 600
+    T = dealer.and_triples(P, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(P, n, SEED, op + 1)
+    mt = dealer.mul_triple(P, n, SEED, op + 2)
+    ref = binary.private_relu(Z.reshape(P, n), T, ra, rb, mt, SEED, op + 3).reshape(Z.shape)
+
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    dA = dev(A)
+    prep = mpc.beaver_conv2d_prepare_products(dev(W), dA, dev(B), dev(C), d)
+    Zp = mpc.beaver_conv2d_prepared_products(dev(X), dA, prep, d, trunc_bits=16)
+    Y = mpc.beaver_conv2d_relu_prepared_products(dev(X), dA, prep, d, SEED, op, trunc_bits=16)
+    mpc.sync_status()
+    assert np.array_equal(host(Zp), Z)
+    assert np.array_equal(host(Y), ref)
+
+
+@pytest.mark.parametrize("P", [3, 8])
+def test_prepared_products_more_parties(mpc, P, rng):
+    b, ci, h, w, co, kh, kw, st, ph, pw = GEOMS[1]
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 94, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    dA = dev(A)
+    prep = mpc.beaver_conv2d_prepare_products(dev(W), dA, dev(B), dev(C), d)
+    Zp = mpc.beaver_conv2d_prepared_products(dev(X), dA, prep, d, trunc_bits=16)
+    mpc.sync_status()
+    assert np.array_equal(host(Zp), Z)
+

@@ -166,16 +166,18 @@ def test_small_stack_pipelined_two_input_buffers(mpc):
 
 
 @pytest.mark.slow
-def test_full_speech_stack_prepared_bit_exact(mpc, full_oracle):
+@pytest.mark.parametrize("products", [False, True])
+def test_full_speech_stack_prepared_bit_exact(mpc, full_oracle, products):
     """The full stack with the convolutions' input-independent half on the
-    dealer (the online-latency schedule) gives the oracle's shares."""
+    dealer (the bench's schedule; with `products` also each party's A_p F, the
+    online-latency schedule) gives the oracle's shares."""
     from paper_2109_00984_b300.nets import PrivateConv1dStack
     x, ws, strides, pads = synth.speech_stack()
     sched = synth.speech_schedule(len(ws))
     net = PrivateConv1dStack(ws, strides, pads, x.shape[2], batch=x.shape[0], algo=mpc.AUTO,
                              weight_ops=sched["weight_op"], seed=sched["seed"],
-                             prepare_weights=True)
-    assert net.prepared
+                             prepare_weights=True, prepare_products=products)
+    assert net.prepared and net.prep_products == products
     Y = net.forward(dev_f64(x), sched)
     torch.cuda.synchronize()
     ref_shares, plain = full_oracle
