@@ -318,6 +318,25 @@ int mpc_beaver_conv2d_relu_prepared(int P, const mpc_conv_desc* d, const uint64_
                                     size_t prep_bytes, uint64_t* Y, int trunc_bits, uint64_t seed,
                                     uint64_t relu_op, void* ws, size_t ws_bytes, void* stream);
 
+/* Beaver convolution, a residual sum and the fused ReLU, two parties (a
+ * ResNet block's second convolution, its shortcut and its ReLU): Y =
+ * ReLU(trunc(conv) + S) with the words of mpc_beaver_conv2d (or _prepared)
+ * followed by mpc_private_relu_fused_add(2, n, Z, S, Y, seed, relu_op); the
+ * ReLU kernel adds the split-K partial sums, C, the truncation and S as it
+ * loads each element.  S device u64 [2][batch][c_out][ho][wo]; Y must not
+ * alias S.  Arguments otherwise as mpc_beaver_conv2d_relu and
+ * mpc_beaver_conv2d_relu_prepared. */
+int mpc_beaver_conv2d_relu_add(int P, const mpc_conv_desc* d, const uint64_t* X,
+                               const uint64_t* W, const uint64_t* A, const uint64_t* B,
+                               const uint64_t* C, const uint64_t* S, uint64_t* Y, int algo,
+                               int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                               size_t ws_bytes, void* stream);
+int mpc_beaver_conv2d_relu_prepared_add(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                        const uint64_t* A, const uint64_t* C, const void* prep,
+                                        size_t prep_bytes, const uint64_t* S, uint64_t* Y,
+                                        int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                                        size_t ws_bytes, void* stream);
+
 /* Prepared products (limb engine): the preparation goes one step further and
  * also computes each party's input-independent product, C'_p = C_p + A_p F
  * with F = W - B opened (App. D.1.1: Z_p = C_p + E B_p + A_p F + [p = 0] E F),

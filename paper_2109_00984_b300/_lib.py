@@ -89,6 +89,12 @@ SIGNATURES = {
     "mpc_beaver_conv2d_relu_prepared_products": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp,
                                                          c_size, c_vp, c_int, c_u64, c_u64, c_vp,
                                                          c_size, c_vp]),
+    "mpc_beaver_conv2d_relu_add": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp, c_vp,
+                                           c_vp, c_vp, c_int, c_int, c_u64, c_u64, c_vp, c_size,
+                                           c_vp]),
+    "mpc_beaver_conv2d_relu_prepared_add": (c_int, [c_int, _P(ConvDesc), c_vp, c_vp, c_vp, c_vp,
+                                                    c_size, c_vp, c_vp, c_int, c_u64, c_u64,
+                                                    c_vp, c_size, c_vp]),
     "mpc_tune_default": (c_int, [_P(Tune)]),
     "mpc_matmul_batched_workspace_size": (c_size, [c_int, c_int, _P(MatmulDesc), c_int, _P(Tune)]),
     "mpc_beaver_matmul_batched": (c_int, [c_int, c_int, _P(MatmulDesc), c_int, _P(Tune), c_int,

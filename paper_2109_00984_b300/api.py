@@ -351,34 +351,51 @@ def beaver_conv2d_relu_prepared_products(X, A, prep, d, seed, relu_op, trunc_bit
 
 
 def beaver_conv2d_relu_prepared(X, A, C, prep, d, seed, relu_op, trunc_bits=0, out=None,
-                                ws=None):
+                                ws=None, add=None):
     """beaver_conv2d_prepared then the fused private ReLU (two parties); equals
-    beaver_conv2d_relu(..., algo=LIMB)."""
+    beaver_conv2d_relu(..., algo=LIMB).  With `add` (shares shaped like the
+    output): the ReLU of the product plus add (a residual connection)."""
     P = X.shape[0]
     ho, wo = conv_out_hw(d)
     Y = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
     need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), LIMB)
     ws = _ws(need, X.device) if ws is None else ws
-    _check(_L().mpc_beaver_conv2d_relu_prepared(P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(C),
-                                                _ptr(prep, "prep", torch.uint8), prep.numel(),
-                                                _ptr(Y), trunc_bits, seed, relu_op,
-                                                _ptr(ws, "ws", torch.uint8), ws.numel(),
-                                                _stream()))
+    if add is None:
+        _check(_L().mpc_beaver_conv2d_relu_prepared(
+            P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(C), _ptr(prep, "prep", torch.uint8),
+            prep.numel(), _ptr(Y), trunc_bits, seed, relu_op, _ptr(ws, "ws", torch.uint8),
+            ws.numel(), _stream()))
+    else:
+        if add.numel() != Y.numel():
+            raise ValueError("add must be shaped like the output")
+        _check(_L().mpc_beaver_conv2d_relu_prepared_add(
+            P, ctypes.byref(d), _ptr(X), _ptr(A), _ptr(C), _ptr(prep, "prep", torch.uint8),
+            prep.numel(), _ptr(add, "add"), _ptr(Y), trunc_bits, seed, relu_op,
+            _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
     return Y
 
 
 def beaver_conv2d_relu(X, W, A, B, C, d, seed, relu_op, algo=PLAIN, trunc_bits=0, out=None,
-                       ws=None):
+                       ws=None, add=None):
     """Beaver convolution then the fused private ReLU (material at relu_op .. relu_op + 3),
-    two parties; equals beaver_conv2d followed by private_relu_fused."""
+    two parties; equals beaver_conv2d followed by private_relu_fused.  With `add`
+    (shares shaped like the output): the ReLU of the product plus add."""
     P = X.shape[0]
     ho, wo = conv_out_hw(d)
     Y = _words((P, d.batch, d.c_out, ho, wo), X.device) if out is None else out
     need = _L().mpc_conv2d_workspace_size(P, ctypes.byref(d), algo)
     ws = _ws(need, X.device) if ws is None else ws
-    _check(_L().mpc_beaver_conv2d_relu(P, ctypes.byref(d), _ptr(X), _ptr(W), _ptr(A), _ptr(B),
-                                       _ptr(C), _ptr(Y), algo, trunc_bits, seed, relu_op,
-                                       _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    if add is None:
+        _check(_L().mpc_beaver_conv2d_relu(P, ctypes.byref(d), _ptr(X), _ptr(W), _ptr(A), _ptr(B),
+                                           _ptr(C), _ptr(Y), algo, trunc_bits, seed, relu_op,
+                                           _ptr(ws, "ws", torch.uint8), ws.numel(), _stream()))
+    else:
+        if add.numel() != Y.numel():
+            raise ValueError("add must be shaped like the output")
+        _check(_L().mpc_beaver_conv2d_relu_add(
+            P, ctypes.byref(d), _ptr(X), _ptr(W), _ptr(A), _ptr(B), _ptr(C), _ptr(add, "add"),
+            _ptr(Y), algo, trunc_bits, seed, relu_op, _ptr(ws, "ws", torch.uint8), ws.numel(),
+            _stream()))
     return Y
 
 

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(256, 3) relu_fused_quad_kernel(i64 n, const u6
 // when the job set was not split.  Same grid and quad layout as
 // relu_fused_quad_kernel.
 __global__ void __launch_bounds__(256, 3) relu_gemm_quad_kernel(const GemmArgs g, u64* Y,
-                                                             u64 seed, u64 op) {
+                                                             u64 seed, u64 op,
+                                                             const u64* __restrict__ S) {
   const i64 n = g.M * g.N;
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 npad = ceil_div(n, (i64)blockDim.x) * blockDim.x;  // uniform trip count per block
@@ -340,6 +341,10 @@ __global__ void __launch_bounds__(256, 3) relu_gemm_quad_kernel(const GemmArgs g
       } else {
         x.v[0] = g.jobs[0].Z[i];
         x.v[1] = g.jobs[1].Z[i];
+      }
+      if (S) {  // a residual sum, added to the truncated product
+        x.v[0] += S[i];
+        x.v[1] += S[n + i];
       }
     }
     const Sh2 y = relu_quad(x, seed, op, i >> 2, j);
@@ -558,13 +563,14 @@ inline uint64_t a2b_rounds(int P) {
 
 }  // namespace
 
-int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s) {
+int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s,
+                        const u64* S) {
   if (g.njobs != 2) return fail(MPC_EUNSUPPORTED, "fused ReLU of a GEMM needs two parties");
   const i64 n = g.M * g.N;
   if (n == 0) return MPC_OK;
   {
     KernelTimer timer("private_relu_fused", s);
-    relu_gemm_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, s>>>(g, Y, seed, op);
+    relu_gemm_quad_kernel<<<grid_for(n, 256, 148 * 8), 256, 0, s>>>(g, Y, seed, op, S);
     if (int rc = check_launch("private_relu_fused (of a GEMM)")) return rc;
   }
   stats_add(9, (uint64_t)MPC_KS_GATES * 16ull * n + (uint64_t)ceil_div(n, 8) + 16ull * n,

@@ -170,6 +170,9 @@ int run_gemm(GemmArgs g, int algo, void* ws, size_t ws_bytes, cudaStream_t s,
 // materialising it: element i of party p is trunc(C_p[i] + sum over splits of
 // the partial sums at the GEMM position of output index i), or Z_p[i] when
 // the job set was not split.  Y [2][M N] receives the ReLU.  Requires njobs = 2.
-int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s);
+// S (may be null): two-party shares [2][M N] added to each truncated output
+// before the ReLU (a residual connection).
+int launch_relu_of_gemm(const GemmArgs& g, u64* Y, u64 seed, u64 op, cudaStream_t s,
+                        const u64* S = nullptr);
 
 }  // namespace mpc

@@ -623,6 +623,23 @@ int mpc_beaver_conv2d_relu(int P, const mpc_conv_desc* d, const uint64_t* X, con
   return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
 }
 
+int mpc_beaver_conv2d_relu_add(int P, const mpc_conv_desc* d, const uint64_t* X,
+                               const uint64_t* W, const uint64_t* A, const uint64_t* B,
+                               const uint64_t* C, const uint64_t* S, uint64_t* Y, int algo,
+                               int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                               size_t ws_bytes, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "convolution + residual + fused ReLU supports P = 2 (got %d)", P);
+  MPC_REQUIRE(S != nullptr && S != Y, "null residual or residual aliasing the output");
+  GemmArgs used{};
+  used.njobs = 0;
+  if (int rc = beaver_conv2d_impl(P, d, X, W, A, B, C, Y, algo, trunc_bits, ws, ws_bytes, stream,
+                                  &used))
+    return rc;
+  if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
+  return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream), (const u64*)S);
+}
+
 size_t mpc_conv2d_prep_size(int P, const mpc_conv_desc* d) {
   i64 ho, wo;
   if (P < 1 || P > MPC_MAX_PARTIES || validate_conv(d, &ho, &wo) != MPC_OK) return 0;
@@ -853,6 +870,27 @@ int mpc_beaver_conv2d_relu_prepared_products(int P, const mpc_conv_desc* d, cons
     return rc;
   if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
   return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream));
+}
+
+int mpc_beaver_conv2d_relu_prepared_add(int P, const mpc_conv_desc* d, const uint64_t* X,
+                                        const uint64_t* A, const uint64_t* C, const void* prep,
+                                        size_t prep_bytes, const uint64_t* S, uint64_t* Y,
+                                        int trunc_bits, uint64_t seed, uint64_t relu_op, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  if (P != 2) return fail(P >= 1 && P <= MPC_MAX_PARTIES ? MPC_EUNSUPPORTED : MPC_EINVAL,
+                          "convolution + residual + fused ReLU supports P = 2 (got %d)", P);
+  MPC_REQUIRE(S != nullptr && S != Y, "null residual or residual aliasing the output");
+  const size_t need = mpc_conv2d_prep_size(P, d);
+  MPC_REQUIRE(prep != nullptr, "null prep buffer");
+  if (need == 0) return fail(MPC_EUNSUPPORTED, "no prepared planes for this shape");
+  if (prep_bytes < need) return fail(MPC_ENOMEM, "prep buffer %zu bytes, need %zu", prep_bytes, need);
+  GemmArgs used{};
+  used.njobs = 0;
+  if (int rc = beaver_conv2d_impl(P, d, X, nullptr, A, nullptr, C, Y, MPC_ALGO_LIMB, trunc_bits,
+                                  ws, ws_bytes, stream, &used, prep))
+    return rc;
+  if (used.njobs != 2) return fail(MPC_EINVAL, "empty convolution");
+  return launch_relu_of_gemm(used, (u64*)Y, seed, relu_op, as_stream(stream), (const u64*)S);
 }
 
 size_t mpc_ring_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int algo) {

@@ -171,11 +171,13 @@ class PrivateResNet18:
         ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d(X, Wsh, A, B, C, d, self.algo, self.frac_bits, ws=ws)
 
-    def conv_relu(self, X, Wsh, stride, pad, op, relu_op, key=None):
-        """A convolution whose output goes straight into a ReLU: one composite call
-        (the ReLU kernel reduces the GEMM's split-K partial sums itself)."""
+    def conv_relu(self, X, Wsh, stride, pad, op, relu_op, key=None, add=None):
+        """A convolution whose output (plus `add`, a residual shortcut, if given)
+        goes straight into a ReLU: one composite call (the ReLU kernel reduces the
+        GEMM's split-K partial sums and adds the shortcut itself)."""
         if not self.fused_relu:
-            return self.relu(self.conv(X, Wsh, stride, pad, op, key), relu_op)
+            Z = self.conv(X, Wsh, stride, pad, op, key)
+            return self.relu(Z if add is None else api.add(Z, add), relu_op)
         P, N, Cin, H, W = X.shape
         Cout, _, k, _ = Wsh.shape[1:]
         d = api.conv_desc(N, Cin, H, W, Cout, k, k, stride, stride, pad, pad)
@@ -189,10 +191,10 @@ class PrivateResNet18:
         if prep is not None:
             ws = self._ws(api.conv2d_workspace_size(P, d, api.LIMB))
             return api.beaver_conv2d_relu_prepared(X, A, C, prep, d, self.seed, relu_op,
-                                                   self.frac_bits, ws=ws)
+                                                   self.frac_bits, ws=ws, add=add)
         ws = self._ws(api.conv2d_workspace_size(P, d, self.algo))
         return api.beaver_conv2d_relu(X, Wsh, A, B, C, d, self.seed, relu_op, self.algo,
-                                      self.frac_bits, ws=ws)
+                                      self.frac_bits, ws=ws, add=add)
 
     def relu(self, X, op):
         P = X.shape[0]
@@ -291,18 +293,14 @@ class PrivateResNet18:
                 _, name, cin, cout, s = layer
                 Y = self.conv_relu(X, self.W[name + ".conv1"], s, 1, ops[name + ".conv1"],
                                    ops[name + ".relu1"], name + ".conv1")
-                Y = self.conv(Y, self.W[name + ".conv2"], 1, 1, ops[name + ".conv2"], name + ".conv2")
                 if s != 1 or cin != cout:
                     S = self.conv(X, self.W[name + ".down"], s, 0, ops[name + ".down"],
                                   name + ".down")
                 else:
                     S = X
-                if self.fused_relu:   # the residual sum folded into the ReLU's load
-                    P = Y.shape[0]
-                    X = api.private_relu_fused(Y.reshape(P, -1), self.seed, ops[name + ".relu2"],
-                                               add=S.reshape(P, -1)).view(Y.shape)
-                else:
-                    X = self.relu(api.add(Y, S), ops[name + ".relu2"])
+                # second convolution, shortcut and ReLU in one composite call
+                X = self.conv_relu(Y, self.W[name + ".conv2"], 1, 1, ops[name + ".conv2"],
+                                   ops[name + ".relu2"], name + ".conv2", add=S)
             elif kind == "avgpool":
                 X = api.global_avgpool(X)
             elif kind == "fc":

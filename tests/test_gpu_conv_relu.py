@@ -164,3 +164,36 @@ def test_prepared_products_more_parties(mpc, P, rng):
     mpc.sync_status()
     assert np.array_equal(host(Zp), Z)
 
+
+
+@pytest.mark.parametrize("geom", GEOMS[:2])
+@pytest.mark.parametrize("mode", ["plain", "limb", "prepared"])
+def test_conv2d_relu_add_matches_oracle(mpc, geom, mode, rng):
+    """Convolution, a residual sum and the ReLU in one call: the oracle's
+    truncated Beaver convolution plus S, then its private ReLU."""
+    b, ci, h, w, co, kh, kw, st, ph, pw = geom
+    P = 2
+    xs, wsh = (b, ci, h, w), (co, ci, kh, kw)
+    X = rng.integers(0, 2 ** 64, (P,) + xs, dtype=np.uint64)
+    W = rng.integers(0, 2 ** 64, (P,) + wsh, dtype=np.uint64)
+    A, B, C = dealer.conv2d_triple(P, xs, wsh, st, ph, SEED, 95, pad_w=pw)
+    Z = truncation.truncate(beaver.beaver_conv2d(X, W, A, B, C, st, ph, pad_w=pw), 16)
+    S = rng.integers(0, 2 ** 64, Z.shape, dtype=np.uint64)
+    n = Z[0].size
+    op = 650
+    T = dealer.and_triples(P, n, 12, SEED, op)
+    ra, rb = dealer.b2a_bits(P, n, SEED, op + 1)
+    mt = dealer.mul_triple(P, n, SEED, op + 2)
+    ref = binary.private_relu((Z + S).reshape(P, n), T, ra, rb, mt, SEED, op + 3).reshape(Z.shape)
+    d = mpc.conv_desc(b, ci, h, w, co, kh, kw, st, st, ph, pw)
+    if mode == "prepared":
+        dA = dev(A)
+        prep = mpc.beaver_conv2d_prepare(dev(W), dA, dev(B), d)
+        Y = mpc.beaver_conv2d_relu_prepared(dev(X), dA, dev(C), prep, d, SEED, op,
+                                            trunc_bits=16, add=dev(S))
+    else:
+        algo = mpc.LIMB if mode == "limb" else mpc.PLAIN
+        Y = mpc.beaver_conv2d_relu(dev(X), dev(W), dev(A), dev(B), dev(C), d, SEED, op,
+                                   algo=algo, trunc_bits=16, add=dev(S))
+    mpc.sync_status()
+    assert np.array_equal(host(Y), ref)
